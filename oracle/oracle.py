@@ -1,0 +1,162 @@
+"""ctypes binding of the serial oracle (``liboracle.so``).
+
+TEST INFRASTRUCTURE ONLY.  Every function here is a thin call into the C++
+oracle; the arithmetic lives in ``rdsplit_oracle.cpp`` (Algorithm 1 and its
+samplers) and ``issa.cpp`` (exact spatial SSA).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_philox4x32.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_philox4x64.argtypes = [_u64p, _u64p, _u64p]
+        for name in ("orc_log_many", "orc_exp_many"):
+            getattr(L, name).argtypes = [_f64p, _f64p, C.c_int64]
+        L.orc_log_factorial_many.argtypes = [_i64p, _f64p, C.c_int64]
+        L.orc_threshold.argtypes = [C.c_double]
+        L.orc_threshold.restype = C.c_uint32
+        L.orc_stream_u32.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, _u32p, C.c_int64]
+        L.orc_stream_u01.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, _f64p, C.c_int64, C.c_int]
+        L.orc_binomial_many.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_double, _i64p, C.c_int64]
+        L.orc_tau.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_double]
+        L.orc_tau.restype = C.c_double
+        L.orc_run.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_int32,
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                              _i32p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_double,
+                              C.c_uint64, C.c_int64]
+        L.orc_run.restype = C.c_int
+        L.orc_issa_run.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _i32p, C.c_double,
+                                   C.c_uint64]
+        L.orc_issa_run.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def philox4x32(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def philox4x64(ctr, key):
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64(np.asarray(ctr, np.uint64), np.asarray(key, np.uint64), out)
+    return out
+
+
+def own_log(x):
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty_like(x)
+    lib().orc_log_many(x.reshape(-1), y.reshape(-1), x.size)
+    return y
+
+
+def own_exp(x):
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty_like(x)
+    lib().orc_exp_many(x.reshape(-1), y.reshape(-1), x.size)
+    return y
+
+
+def log_factorial(k):
+    k = np.ascontiguousarray(k, np.int64)
+    y = np.empty(k.shape, np.float64)
+    lib().orc_log_factorial_many(k.reshape(-1), y.reshape(-1), k.size)
+    return y
+
+
+def threshold(y: float) -> int:
+    return int(lib().orc_threshold(float(y)))
+
+
+def stream_u32(seed, tet, period, purpose, species, n):
+    out = np.zeros(n, np.uint32)
+    lib().orc_stream_u32(seed, tet, period, purpose, species, out, n)
+    return out
+
+
+def stream_u01(seed, tet, period, purpose, species, n, open0=False):
+    out = np.zeros(n, np.float64)
+    lib().orc_stream_u01(seed, tet, period, purpose, species, out, n, int(open0))
+    return out
+
+
+def binomial_many(n: int, p: float, count: int, seed: int = 1, period: int = 0):
+    out = np.zeros(count, np.int64)
+    lib().orc_binomial_many(seed, period, n, p, out, count)
+    return out
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _model_arrays(model):
+    S = model.n_species
+    R = model.n_reactions
+    D = np.ascontiguousarray(model.D, np.float64)
+    lhs = np.ascontiguousarray(model.lhs, np.int32).reshape(R, S) if R else np.zeros((1, S), np.int32)
+    rhs = np.ascontiguousarray(model.rhs, np.int32).reshape(R, S) if R else np.zeros((1, S), np.int32)
+    k = np.ascontiguousarray(model.k, np.float64) if R else np.zeros(1)
+    mask = None if model.mask is None else np.ascontiguousarray(model.mask, np.uint8)
+    return S, R, D, lhs, rhs, k, mask
+
+
+def tau(mesh, model) -> float:
+    S, R, D, *_ = _model_arrays(model)
+    return lib().orc_tau(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D,
+                         float(model.tau_scale))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def run(mesh, model, counts, t_end: float, seed: int, t0: float = 0.0, period0: int = 0,
+        max_periods: int = -1):
+    """Algorithm 1 from ``t0`` towards ``t_end`` (at most ``max_periods``
+    periods).  Returns (counts [T][S] int32, t, period)."""
+    S, R, D, lhs, rhs, k, mask = _model_arrays(model)
+    c = np.ascontiguousarray(counts, np.int32).copy()
+    assert c.shape == (mesh.n_tets, S)
+    t = C.c_double(t0)
+    p = C.c_int64(period0)
+    rc = lib().orc_run(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
+                       lhs.ctypes.data, rhs.ctypes.data, k.ctypes.data, _ptr(mask),
+                       float(model.tau_scale), c, C.byref(t), C.byref(p), float(t_end),
+                       int(seed), int(max_periods))
+    if rc != 0:
+        raise OracleError(f"orc_run failed with code {rc}")
+    return c, t.value, p.value
+
+
+def issa_run(mesh, model, counts, t_end: float, seed: int):
+    """Exact whole-mesh SSA to ``t_end``; returns counts [T][S]."""
+    S, R, D, lhs, rhs, k, mask = _model_arrays(model)
+    c = np.ascontiguousarray(counts, np.int32).copy()
+    rc = lib().orc_issa_run(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
+                            lhs.ctypes.data, rhs.ctypes.data, k.ctypes.data, _ptr(mask), c,
+                            float(t_end), int(seed))
+    if rc != 0:
+        raise OracleError(f"orc_issa_run failed with code {rc}")
+    return c

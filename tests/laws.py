@@ -1,0 +1,97 @@
+"""Exact laws used to pin the oracle (test helpers, numpy/scipy only).
+
+Nothing here calls the oracle or the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import expm
+
+
+def face_rates(mesh, D: float) -> np.ndarray:
+    """Per-molecule hop rate t -> adj[t][f]: D * A_tf / (V_t * dist_tf)
+    (the rate definition of the workload; 0 on the boundary)."""
+    g = np.zeros_like(mesh.area)
+    inner = mesh.adj >= 0
+    g[inner] = mesh.area[inner] / (mesh.vol[:, None] * mesh.dist)[inner]
+    return D * g
+
+
+def one_period_matrix(mesh, D: float, tau_k: float) -> np.ndarray:
+    """Transition matrix of one molecule over one period of pure diffusion:
+    it leaves t through face f with probability tau_k * rate_tf (Eq. 1 text:
+    the transfer probability over a period is zeta = tau * d; the direction
+    is multinomial with weights proportional to the face rates)."""
+    T = mesh.n_tets
+    rate = face_rates(mesh, D)
+    M = np.zeros((T, T))
+    for t in range(T):
+        for f in range(4):
+            u = mesh.adj[t, f]
+            if u >= 0:
+                M[t, u] += tau_k * rate[t, f]
+        M[t, t] = 1.0 - M[t].sum()
+    return M
+
+
+def birth_death_ABC(a0: int, b0: int, c_fwd: float, c_bwd: float, C0: int, t: float) -> np.ndarray:
+    """Law of C(t) for A+B <-> C in one well-mixed volume with A+C=a0,
+    B+C=b0 conserved: a birth-death chain with birth rate
+    c_fwd*(a0-C)(b0-C) and death rate c_bwd*C, solved by a matrix
+    exponential of its generator."""
+    n = min(a0, b0) + 1
+    Q = np.zeros((n, n))
+    for c in range(n):
+        up = c_fwd * (a0 - c) * (b0 - c)
+        dn = c_bwd * c
+        if c + 1 < n:
+            Q[c, c + 1] = up
+        if c > 0:
+            Q[c, c - 1] = dn
+        Q[c, c] = -(Q[c].sum())
+    p0 = np.zeros(n)
+    p0[C0] = 1.0
+    return p0 @ expm(Q * t)
+
+
+def chi2_pvalue(observed: np.ndarray, expected_p: np.ndarray, min_expected: float = 5.0) -> float:
+    """Pearson chi-square goodness of fit with bins pooled so every expected
+    count is at least ``min_expected``."""
+    from scipy.stats import chi2
+    n = observed.sum()
+    e = expected_p * n
+    obs_b, exp_b = [], []
+    o_acc = e_acc = 0.0
+    for o, x in zip(observed, e):
+        o_acc += o
+        e_acc += x
+        if e_acc >= min_expected:
+            obs_b.append(o_acc)
+            exp_b.append(e_acc)
+            o_acc = e_acc = 0.0
+    if e_acc > 0 and exp_b:
+        obs_b[-1] += o_acc
+        exp_b[-1] += e_acc
+    obs_b = np.array(obs_b)
+    exp_b = np.array(exp_b)
+    stat = ((obs_b - exp_b) ** 2 / exp_b).sum()
+    dof = max(len(obs_b) - 1, 1)
+    return float(chi2.sf(stat, dof))
+
+
+def two_tet_mesh(vol=(1e-19, 1e-19), area=1e-13, dist=2e-7):
+    """Two tets sharing face 0, all other faces on the boundary."""
+    from paper_1512_03126_gb300.inputs import Mesh
+    adj = np.array([[1, -1, -1, -1], [0, -1, -1, -1]], np.int32)
+    a = np.zeros((2, 4))
+    a[:, 0] = area
+    d = np.zeros((2, 4))
+    d[:, 0] = dist
+    return Mesh(adj=adj, vol=np.array(vol, np.float64), area=a, dist=d,
+                centroid=np.array([[0, 0, 0], [dist, 0, 0]], np.float64), shape=(), size=(1, 1, 1))
+
+
+def one_tet_mesh(vol=1e-19):
+    from paper_1512_03126_gb300.inputs import Mesh
+    return Mesh(adj=np.full((1, 4), -1, np.int32), vol=np.array([vol]), area=np.full((1, 4), 1e-13),
+                dist=np.zeros((1, 4)), centroid=np.zeros((1, 3)), shape=(), size=(1, 1, 1))

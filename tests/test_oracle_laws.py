@@ -1,0 +1,189 @@
+"""Pins of the serial oracle (Algorithm 1) against what the mathematics and
+the paper fix: conservation, the exact law of pure diffusion under operator
+splitting, exact reaction laws, the mean-corrected transfer of Eq. 2-3, the
+continuum spreading rate, and a brute-force exact spatial SSA."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import binom
+
+from paper_1512_03126_gb300 import inputs as I
+from tests.laws import (birth_death_ABC, chi2_pvalue, one_period_matrix, one_tet_mesh,
+                        two_tet_mesh)
+
+
+def _src(counts):
+    return int(np.nonzero(counts.sum(1))[0][0])
+
+
+def test_conservation_and_sign(oracle):
+    """Pure diffusion moves molecules between tets and never creates or
+    destroys them; counts stay >= 0 (Sec. II.A, transfer-based diffusion)."""
+    w = I.config_diffusion_3072()
+    c = w.counts.copy()
+    t, per = 0.0, 0
+    for _ in range(5):
+        c, t, per = oracle.run(w.mesh, w.model, c, w.t_end, w.seed, t0=t, period0=per, max_periods=20)
+        assert c.sum() == 6000 and c.min() >= 0
+    assert per == 100
+
+
+def test_period_rule_and_alignment(oracle):
+    """tau = 1 / max(D_s * sum_f A/(V dist)) (Algorithm 1, precompute); the last
+    period is shortened to land on t_end (Step 1)."""
+    w = I.config_diffusion_3072()
+    tau = oracle.tau(w.mesh, w.model)
+    g = np.where(w.mesh.adj >= 0, w.mesh.area / (w.mesh.vol[:, None] * np.where(w.mesh.dist > 0, w.mesh.dist, 1)), 0)
+    assert tau == pytest.approx(1.0 / (1e-12 * g.sum(1).max()), rel=1e-12)
+    # 4.623e-4 s on the 1 um 8^3 Kuhn cube with D = 1e-12 m^2/s
+    assert tau == pytest.approx(4.623e-4, rel=1e-3)
+    c, t, per = oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed)
+    assert t == w.t_end and per == math.ceil(w.t_end / tau)
+
+
+@pytest.mark.parametrize("n0", [6, 300])
+def test_exact_law_of_pure_diffusion(oracle, n0):
+    """With N-bar = N each molecule independently takes one step of the
+    period matrix M per period (leave with probability zeta = tau*d, direction
+    multinomial by face weight), so the count in tet u after k periods is
+    Binomial(N0, (e_src M^k)_u) and the pooled positions are multinomial.
+    n0 = 6 exercises the one-draw-per-molecule path, n0 = 300 the binomial +
+    conditional-binomial path."""
+    m = I.cube(2, 0.5e-6, 0.2, 7)
+    model = I.diffusion_model(1e-12)
+    c0 = np.zeros((m.n_tets, 1), np.int32)
+    src = 17
+    c0[src, 0] = n0
+    tau = oracle.tau(m, model)
+    k = 6
+    p = np.linalg.matrix_power(one_period_matrix(m, 1e-12, tau), k)[src]
+    seeds = 3000
+    finals = np.stack([oracle.run(m, model, c0, np.inf, s, max_periods=k)[0][:, 0] for s in range(seeds)])
+    assert np.all(finals.sum(1) == n0)
+    pooled = finals.sum(0)
+    assert chi2_pvalue(pooled, p) > 1e-4
+    u = int(np.argmax(p))
+    obs = np.bincount(finals[:, u], minlength=n0 + 1)
+    assert chi2_pvalue(obs, binom.pmf(np.arange(n0 + 1), n0, p[u])) > 1e-4
+
+
+def test_zeta_one_empties_the_fastest_tet(oracle):
+    """On a regular mesh zeta = 1 in the fastest tets (Sec. II.A): every
+    molecule there leaves in one period, in both sampler paths."""
+    m = I.cube(3, 1e-6, 0.0, 0)
+    model = I.diffusion_model(1e-12)
+    g = np.where(m.adj >= 0, m.area / (m.vol[:, None] * np.where(m.dist > 0, m.dist, 1)), 0).sum(1)
+    fast = int(np.nonzero(g == g.max())[0][0])
+    for n0 in (7, 500):
+        c0 = np.zeros((m.n_tets, 1), np.int32)
+        c0[fast, 0] = n0
+        for s in range(20):
+            c, _, _ = oracle.run(m, model, c0, np.inf, s, max_periods=1)
+            assert c[fast, 0] == 0 and c.sum() == n0
+
+
+def test_first_order_decay_is_exactly_binomial(oracle):
+    """Per-tet SSA is exact for A -> 0 and diffusion neither creates nor
+    destroys molecules, so survivors ~ Binomial(N0, exp(-k t)) exactly."""
+    m = I.cube(2, 0.5e-6, 0.2, 7)
+    kdec = 20.0
+    model = I.Model(D=np.array([1e-12]), lhs=np.array([[1]], np.int32), rhs=np.array([[0]], np.int32),
+                    k=np.array([kdec]))
+    c0 = np.zeros((m.n_tets, 1), np.int32)
+    c0[5, 0] = 200
+    t_end = math.log(2.0) / kdec
+    tot = np.array([oracle.run(m, model, c0, t_end, s)[0].sum() for s in range(3000)])
+    obs = np.bincount(tot, minlength=201)
+    assert chi2_pvalue(obs, binom.pmf(np.arange(201), 200, math.exp(-kdec * t_end))) > 1e-4
+
+
+def _abc(k1_pair_rate, k2, vol):
+    """A + B <-> C with the given per-pair forward rate (1/s) in a tet of
+    volume ``vol``, plus a diffusing spectator Z that fixes tau."""
+    nav = 6.02214076e23 * vol * 1e3
+    lhs = np.array([[1, 1, 0, 0], [0, 0, 1, 0]], np.int32)
+    rhs = np.array([[0, 0, 1, 0], [1, 1, 0, 0]], np.int32)
+    return I.Model(D=np.array([0.0, 0.0, 0.0, 1e-12]), lhs=lhs, rhs=rhs,
+                   k=np.array([k1_pair_rate * nav, k2]), tau_scale=0.1)
+
+
+@pytest.mark.parametrize("two_tets", [False, True])
+def test_reversible_binding_matches_master_equation(oracle, two_tets):
+    """A + B <-> C in one tet: the law of C(t) is the birth-death chain of the
+    chemical master equation.  With one tet there is a single period; with
+    two tets and a diffusing spectator the SSA restarts every period, which
+    must not change the law (memoryless events)."""
+    vol = 1e-19
+    model = _abc(0.5, 2.0, vol)
+    mesh = two_tet_mesh((vol, vol)) if two_tets else one_tet_mesh(vol)
+    c0 = np.zeros((mesh.n_tets, 4), np.int32)
+    c0[0, 0], c0[0, 1] = 8, 6
+    t_end = 0.3
+    if two_tets:
+        assert oracle.tau(mesh, model) < t_end / 5
+    C = np.array([oracle.run(mesh, model, c0, t_end, s)[0][0, 2] for s in range(4000)])
+    law = birth_death_ABC(8, 6, 0.5, 2.0, 0, t_end)
+    assert chi2_pvalue(np.bincount(C, minlength=law.size), law) > 1e-4
+
+
+def test_mean_corrected_transfer(oracle):
+    """Eq. 2-3: the number leaving a tet over a period is drawn from the mean
+    occupancy N-bar during the period, not N at its end.  With a zero-order
+    influx of rate a into a tet holding N0, E[N-bar] = N0 + a tau / 2, so
+    E[n] = zeta (N0 + a tau / 2); first-order splitting would give
+    zeta (N0 + a tau)."""
+    vol = 1e-19
+    mesh = two_tet_mesh((vol, vol))
+    D = 1e-12
+    zeta = 0.5
+    model0 = I.diffusion_model(D)
+    model0.tau_scale = zeta
+    tau = oracle.tau(mesh, model0)
+    a_tau = 20.0
+    k_in = a_tau / (tau * 6.02214076e23 * vol * 1e3)
+    mask = np.array([[1, 0]], np.uint8)
+    model = I.Model(D=np.array([D]), lhs=np.zeros((1, 1), np.int32), rhs=np.ones((1, 1), np.int32),
+                    k=np.array([k_in]), mask=mask, tau_scale=zeta)
+    c0 = np.array([[5], [0]], np.int32)
+    n = np.array([oracle.run(mesh, model, c0, np.inf, s, max_periods=1)[0][1, 0] for s in range(20000)])
+    expect = zeta * (5 + a_tau / 2)
+    se = n.std() / math.sqrt(n.size)
+    assert abs(n.mean() - expect) < 4 * se
+    assert abs(n.mean() - zeta * (5 + a_tau)) > 20 * se
+
+
+def test_point_source_spreads_at_6Dt(oracle):
+    """Volume diffusion speed (Sec. III.A): from a point source the mean
+    squared displacement grows as 6 D t in 3-D (before the walls matter)."""
+    m = I.cube(12, 3e-6, 0.2, 9)
+    model = I.diffusion_model(1e-12)
+    c0 = I.point_source(m, 1, 0, 2000)
+    src = _src(c0)
+    t_end = 0.055
+    c, t, _ = oracle.run(m, model, c0, t_end, 5)
+    msd = (c[:, 0][:, None] * (m.centroid - m.centroid[src]) ** 2).sum() / 2000
+    assert 0.9 < msd / (6e-12 * t_end) < 1.1
+
+
+def test_agrees_with_exact_spatial_ssa(oracle):
+    """Brute force: on a 12-tet mesh with diffusion and A + B <-> C the
+    per-tet means of operator splitting (tau scaled to 0.1) match the exact
+    whole-mesh SSA within 4.5 standard errors."""
+    m = I.kuhn_box(1, 1, 2, (0.5e-6, 0.5e-6, 1.0e-6), 0.0, 0)
+    nav = 6.02214076e23 * m.vol.mean() * 1e3
+    lhs = np.array([[1, 1, 0], [0, 0, 1]], np.int32)
+    rhs = np.array([[0, 0, 1], [1, 1, 0]], np.int32)
+    model = I.Model(D=np.array([1e-12, 0.5e-12, 0.2e-12]), lhs=lhs, rhs=rhs,
+                    k=np.array([2.0 * nav, 5.0]), tau_scale=0.1)
+    c0 = np.zeros((m.n_tets, 3), np.int32)
+    c0[0] = (20, 15, 0)
+    t_end = 0.05
+    n = 3000
+    os_ = np.stack([oracle.run(m, model, c0, t_end, s)[0] for s in range(n)]).astype(float)
+    ex = np.stack([oracle.issa_run(m, model, c0, t_end, 10**6 + s) for s in range(n)]).astype(float)
+    diff = os_.mean(0) - ex.mean(0)
+    se = np.sqrt(os_.var(0) / n + ex.var(0) / n) + 1e-12
+    assert np.all(np.abs(diff) < 4.5 * se + 1e-9)
+    # the two are genuinely stochastic and both moved mass
+    assert ex[:, 0, :].mean() < 20
