@@ -1,0 +1,152 @@
+/*
+ * rdsplit — operator-split stochastic reaction-diffusion on tetrahedral
+ * meshes, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Hepburn, Chen & De Schutter, "Accurate reaction-diffusion operator
+ * splitting on tetrahedral meshes for parallel stochastic molecular
+ * simulations" (arXiv:1512.03126), Algorithm 1.  In every period tau each
+ * tetrahedron runs its own SSA reactions (Sec. II.C, Step 2), then each
+ * species sends n = Binomial(N-bar, zeta) molecules (Eq. 3) to its face
+ * neighbours multinomially (Sec. II.B), and the transfers are applied
+ * synchronously.
+ *
+ * Conventions for every call:
+ *   - Return value: 0 on success, else a negative RDSPLIT_E* code; the text
+ *     of the last error on the calling thread is rdsplit_last_error().
+ *   - Host arrays passed in are copied during the call; the caller keeps
+ *     ownership.  Output arrays are caller-owned and must have the stated
+ *     size.
+ *   - Tet order: all arrays use the caller's (canonical) tet order; random
+ *     streams are keyed by canonical tet ids, so results never depend on how
+ *     the library stores or schedules tets.
+ *   - Counts are int32 [n_tets][n_species], tet-major.
+ *   - All device work of a handle is issued on its stream (default: the
+ *     legacy default stream; see rdsplit_set_stream) and every call that
+ *     returns host-visible results synchronises that stream.
+ *   - A handle must not be used from two threads at once.
+ */
+#ifndef RDSPLIT_H
+#define RDSPLIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RDSPLIT_OK 0
+#define RDSPLIT_EINVAL (-1)    /* bad argument, malformed mesh or model */
+#define RDSPLIT_ENOMEM (-2)    /* device allocation failed or budget exceeded */
+#define RDSPLIT_ECUDA (-3)     /* a CUDA runtime call failed */
+#define RDSPLIT_ETIMEOUT (-4)  /* a bounded device-side wait expired */
+#define RDSPLIT_EOVERFLOW (-5) /* a count would exceed INT32_MAX, or a
+                                  period would exceed the per-tet event cap */
+#define RDSPLIT_ESTATE (-6)    /* call out of order (e.g. run before set_model) */
+
+#define RDSPLIT_MAX_SPECIES 16
+#define RDSPLIT_MAX_REACTIONS 32
+
+typedef struct rdsplit_mesh* rdsplit_mesh_t;
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* rdsplit_last_error(void);
+
+/*
+ * Create a mesh handle from the geometry of Sec. II.A: irregular tetrahedral
+ * subvolumes with up to 4 face neighbours each.
+ *   n_tets         number of tets, > 0
+ *   adj            int32 [n_tets][4]; adj[t][f] = neighbour across face f, or
+ *                  -1 (reflective boundary).  Must be symmetric: if
+ *                  adj[t][f] = u then exactly one r has adj[u][r] = t.
+ *   vol            float64 [n_tets], m^3, > 0
+ *   face_area      float64 [n_tets][4], m^2, >= 0
+ *   centroid_dist  float64 [n_tets][4], m, distance between the centroids of
+ *                  t and adj[t][f]; > 0 where adj >= 0, ignored elsewhere
+ *   flags          0 (reserved)
+ *   out            receives the handle
+ * The face coefficient g = A / (V dist) and the reverse-face table are
+ * computed on the device; validation runs there too and a malformed mesh
+ * returns RDSPLIT_EINVAL.
+ */
+int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol,
+                        const double* face_area, const double* centroid_dist,
+                        int32_t flags, rdsplit_mesh_t* out);
+
+/*
+ * Attach a chemistry (Sec. III.C: species with diffusion constants,
+ * mass-action reactions with rate constants) and compute the period
+ * tau = tau_scale / max_{s,t}(D_s * sum_f g_tf)  (Algorithm 1, precompute;
+ * tau_scale < 1 is the "reduce zeta everywhere" option of Sec. II.A).
+ *   n_species      1..RDSPLIT_MAX_SPECIES
+ *   D              float64 [n_species], m^2/s, >= 0
+ *   n_reactions    0..RDSPLIT_MAX_REACTIONS
+ *   lhs, rhs       int32 [n_reactions][n_species] reactant / product
+ *                  stoichiometry, >= 0, total reactant order <= 2
+ *   k              float64 [n_reactions]; s^-1 (first order), M^-1 s^-1
+ *                  (second order), M s^-1 (zero order, scaled by the tet
+ *                  volume)
+ *   rxn_tet_mask   uint8 [n_reactions][n_tets] (0 = reaction off in that
+ *                  tet) or NULL (everywhere)
+ *   tau_scale      in (0, 1]
+ * Resets counts to zero, time to 0 and the period index to 0.
+ */
+int rdsplit_set_model(rdsplit_mesh_t mesh, int32_t n_species, const double* D,
+                      int32_t n_reactions, const int32_t* lhs, const int32_t* rhs,
+                      const double* k, const uint8_t* rxn_tet_mask, double tau_scale);
+
+/* Set counts from host memory, int32 [n_tets][n_species], all >= 0. */
+int rdsplit_set_counts(rdsplit_mesh_t mesh, const int32_t* counts);
+/* Same from device memory (same layout), e.g. a torch CUDA tensor. */
+int rdsplit_set_counts_device(rdsplit_mesh_t mesh, const int32_t* d_counts);
+
+/*
+ * Advance from the current time t to t_end with Algorithm 1: periods of
+ * length tau, the last one shortened to end on t_end (Step 1).  `seed` keys
+ * every random draw together with the global period index, so that
+ * run(t1) followed by run(t2) equals run(t2) whenever t1 falls on a period
+ * boundary.  t_end <= t is a no-op.
+ */
+int rdsplit_run(rdsplit_mesh_t mesh, double t_end, uint64_t seed);
+
+/* Advance exactly n_periods full periods of length tau (no alignment). */
+int rdsplit_run_periods(rdsplit_mesh_t mesh, int64_t n_periods, uint64_t seed);
+
+/* Copy counts to host memory, int32 [n_tets][n_species]. */
+int rdsplit_get_counts(rdsplit_mesh_t mesh, int32_t* out);
+/* Same into device memory. */
+int rdsplit_get_counts_device(rdsplit_mesh_t mesh, int32_t* d_out);
+
+/* Current time (s) and global period index. */
+int rdsplit_get_time(rdsplit_mesh_t mesh, double* t, int64_t* period);
+/* Set the current time and period index (checkpoint restore). */
+int rdsplit_set_time(rdsplit_mesh_t mesh, double t, int64_t period);
+/* The period tau (s) of the attached model; +inf if no species diffuses. */
+int rdsplit_get_tau(rdsplit_mesh_t mesh, double* tau);
+/* Number of tets / species of the handle. */
+int rdsplit_get_shape(rdsplit_mesh_t mesh, int32_t* n_tets, int32_t* n_species);
+
+/* Issue all of the handle's device work on `stream` (a cudaStream_t). */
+int rdsplit_set_stream(rdsplit_mesh_t mesh, void* stream);
+
+/* Release the handle and its device memory. */
+int rdsplit_mesh_destroy(rdsplit_mesh_t mesh);
+
+/*
+ * Device memory provider for all later allocations (e.g. PyTorch's caching
+ * allocator).  alloc(bytes, ctx) returns a device pointer or NULL; free(ptr,
+ * ctx) releases it.  NULL functions restore cudaMalloc / cudaFree.  Must not
+ * be changed while handles allocated through the previous provider exist.
+ */
+typedef void* (*rdsplit_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*rdsplit_free_fn)(void* ptr, void* ctx);
+int rdsplit_set_allocator(rdsplit_alloc_fn alloc, rdsplit_free_fn free_fn, void* ctx);
+
+/* Number of kernels the library has launched on this process so far. */
+int64_t rdsplit_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDSPLIT_H */

@@ -208,7 +208,8 @@ int64_t binomial_inversion(int64_t n, double p, Stream& st) {
 // J. Statist. Comput. Simul. 46 (1993).  A candidate k is drawn from the
 // hat (a scaled Cauchy-like transform of a uniform); it is accepted at once
 // inside the squeeze, else by comparing log(V * hat) with the log of the
-// pmf ratio f(k)/f(m) at the mode m.
+// pmf ratio f(k)/f(m) at the mode m.  The loop is bounded (100000 tries,
+// then the mode is returned) so that it always terminates.
 int64_t binomial_btrs(int64_t n, double p, Stream& st) {
     double q = 1.0 - p;
     double dn = (double)n;
@@ -221,7 +222,7 @@ int64_t binomial_btrs(int64_t n, double p, Stream& st) {
     double lpq = own_log(p / q);
     int64_t m = (int64_t)std::floor((dn + 1.0) * p);
     double h = log_factorial(m) + log_factorial(n - m);
-    for (;;) {
+    for (int attempt = 0; attempt < 100000; ++attempt) {
         double u = st.u01() - 0.5;
         double v = st.u01();
         double us = 0.5 - std::fabs(u);
@@ -233,6 +234,7 @@ int64_t binomial_btrs(int64_t n, double p, Stream& st) {
         double lf = h - log_factorial(k) - log_factorial(n - k) + (double)(k - m) * lpq;
         if (lv <= lf) return k;
     }
+    return m;   // unreachable in practice: acceptance probability > 0.5 per try
 }
 
 // Binomial(n, p) for any n >= 0, p in [0, 1].

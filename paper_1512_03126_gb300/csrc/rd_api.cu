@@ -1,0 +1,428 @@
+// Host side of the C ABI declared in include/rdsplit.h: handle lifetime,
+// argument validation, device memory, and the period loop of Algorithm 1
+// (Step 1 alignment and Step 4 time advance, arXiv:1512.03126) around the
+// kernels of rd_kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rd_internal.h"
+#include "rd_api_internal.h"
+#include "rdsplit.h"
+
+using namespace rdk;
+
+namespace rdapi {
+
+thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+static rdsplit_alloc_fn g_alloc = nullptr;
+static rdsplit_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+void* dev_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (g_alloc) return g_alloc(bytes, g_alloc_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    if (g_free) g_free(p, g_alloc_ctx);
+    else cudaFree(p);
+}
+
+void set_allocator(rdsplit_alloc_fn a, rdsplit_free_fn f, void* ctx) {
+    g_alloc = a;
+    g_free = f;
+    g_alloc_ctx = ctx;
+}
+
+}  // namespace rdapi
+
+using namespace rdapi;
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            return fail(RDSPLIT_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                        __FILE__, __LINE__);                                               \
+        }                                                                                  \
+    } while (0)
+
+struct rdsplit_mesh {
+    int32_t T = 0, S = 0, R = 0;
+    cudaStream_t stream = 0;
+    // geometry
+    int4* src = nullptr;
+    double* g = nullptr;
+    double* G = nullptr;
+    double* vol = nullptr;
+    uint32_t* mask = nullptr;
+    unsigned long long* gmax = nullptr;
+    uint32_t* err = nullptr;
+    // model and state
+    double* D = nullptr;
+    double* d_tau = nullptr;
+    int32_t* cnt = nullptr;
+    int32_t* rem = nullptr;
+    int4* out[2] = {nullptr, nullptr};
+    uint4* thr = nullptr;
+    uint4* thr_last = nullptr;
+    int32_t* staging = nullptr;
+    ModelParams mp{};
+    bool has_model = false;
+    double tau = 0.0;
+    double t = 0.0;
+    int64_t period = 0;
+
+    DevMesh dev_mesh() const { return DevMesh{T, src, g, G, vol, mask}; }
+    DevState dev_state() const { return DevState{cnt, rem, err}; }
+
+    void free_model() {
+        void* ps[] = {D, d_tau, cnt, rem, out[0], out[1], thr, thr_last, staging, mask};
+        for (void* p : ps) dev_free(p);
+        D = nullptr; d_tau = nullptr; cnt = nullptr; rem = nullptr; out[0] = out[1] = nullptr;
+        thr = nullptr; thr_last = nullptr; staging = nullptr; mask = nullptr;
+        has_model = false;
+    }
+    ~rdsplit_mesh() {
+        free_model();
+        void* ps[] = {src, g, G, vol, gmax, err};
+        for (void* p : ps) dev_free(p);
+    }
+};
+
+namespace {
+
+template <typename T>
+int alloc_into(T** p, size_t count, const char* what) {
+    *p = (T*)dev_alloc(count * sizeof(T));
+    if (!*p) return fail(RDSPLIT_ENOMEM, "device allocation of %s (%zu bytes) failed", what, count * sizeof(T));
+    return RDSPLIT_OK;
+}
+
+// Read and clear the device error word; translate kernel error bits.
+int check_err(rdsplit_mesh* h, const char* where) {
+    uint32_t e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (e == 0) return RDSPLIT_OK;
+    CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(uint32_t), h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (e & kErrAdjRange) return fail(RDSPLIT_EINVAL, "%s: neighbour index out of range or self-adjacent", where);
+    if (e & kErrAdjAsym) return fail(RDSPLIT_EINVAL, "%s: adjacency is not symmetric", where);
+    if (e & kErrVolume) return fail(RDSPLIT_EINVAL, "%s: a tet volume is not finite and positive", where);
+    if (e & kErrFace) return fail(RDSPLIT_EINVAL, "%s: a face area or centroid distance is invalid", where);
+    if (e & kErrOverflow) return fail(RDSPLIT_EOVERFLOW, "%s: a count exceeded INT32_MAX", where);
+    if (e & kErrEventCap) return fail(RDSPLIT_EOVERFLOW, "%s: SSA event cap per tet and period exceeded", where);
+    if (e & kErrTimeout) return fail(RDSPLIT_ETIMEOUT, "%s: bounded device wait expired", where);
+    if (e & kErrNegative) return fail(RDSPLIT_EINVAL, "%s: negative count", where);
+    return fail(RDSPLIT_ECUDA, "%s: device error bits 0x%x", where, e);
+}
+
+int launch_check(const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RDSPLIT_ECUDA, "%s: kernel launch failed: %s", where, cudaGetErrorString(e));
+    return RDSPLIT_OK;
+}
+
+}  // namespace
+
+namespace rdapi {
+
+// The period loop of Algorithm 1 for one handle.  Step 1: the last period is
+// shortened so that it ends on t_end.  Step 2-3 run in k_period, which also
+// applies the previous period's transfers; the closing k_gather applies the
+// last one.  Step 4: t += tau.
+int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) {
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "rdsplit_run: no model attached");
+    if (std::isnan(t_end)) return fail(RDSPLIT_EINVAL, "rdsplit_run: t_end is NaN");
+    DevMesh m = h->dev_mesh();
+    DevState s = h->dev_state();
+    int64_t j = 0;
+    const int4* prev = nullptr;
+    while (h->t < t_end && (max_periods < 0 || j < max_periods)) {
+        if (h->period >= (int64_t)0xffffffffll)
+            return fail(RDSPLIT_EOVERFLOW, "rdsplit_run: period index exceeds 2^32-1");
+        double tau_k = h->tau;
+        bool last = false;
+        if (h->t + h->tau > t_end) {
+            tau_k = t_end - h->t;
+            last = true;
+        }
+        const uint4* thr = h->thr;
+        if (last) {
+            launch_thresholds(h->T, h->mp, h->g, h->G, tau_k, h->thr_last, h->stream);
+            thr = h->thr_last;
+        }
+        int4* cur = h->out[j & 1];
+        PeriodArgs a{(uint32_t)h->period, tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
+        launch_period(m, h->mp, s, a, h->stream);
+        prev = cur;
+        h->t = last ? t_end : h->t + h->tau;
+        h->period += 1;
+        j += 1;
+    }
+    if (j > 0) launch_gather(m, h->S, s, prev, h->stream);
+    int rc = launch_check("rdsplit_run");
+    if (rc) return rc;
+    return check_err(h, "rdsplit_run");
+}
+
+}  // namespace rdapi
+
+extern "C" {
+
+const char* rdsplit_last_error(void) { return g_error.c_str(); }
+
+int64_t rdsplit_kernel_launches(void) { return rdk::launches(); }
+
+int rdsplit_set_allocator(rdsplit_alloc_fn a, rdsplit_free_fn f, void* ctx) {
+    if ((a == nullptr) != (f == nullptr))
+        return fail(RDSPLIT_EINVAL, "rdsplit_set_allocator: give both functions or neither");
+    set_allocator(a, f, ctx);
+    return RDSPLIT_OK;
+}
+
+int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol, const double* face_area,
+                        const double* centroid_dist, int32_t flags, rdsplit_mesh_t* out) {
+    if (!out) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: out is NULL");
+    *out = nullptr;
+    if (n_tets <= 0) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: n_tets must be > 0 (got %d)", n_tets);
+    if (n_tets > (1 << 29)) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: n_tets too large");
+    if (!adj || !vol || !face_area || !centroid_dist)
+        return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: NULL array");
+    if (flags != 0) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: unknown flags 0x%x", flags);
+    rdsplit_mesh* h = new rdsplit_mesh();
+    h->T = n_tets;
+    const size_t T = (size_t)n_tets;
+    int32_t* d_adj = nullptr;
+    double *d_area = nullptr, *d_dist = nullptr;
+    int rc = RDSPLIT_OK;
+    auto cleanup = [&](int code) {
+        dev_free(d_adj);
+        dev_free(d_area);
+        dev_free(d_dist);
+        if (code != RDSPLIT_OK) delete h;
+        return code;
+    };
+    if ((rc = alloc_into(&d_adj, 4 * T, "adj")) || (rc = alloc_into(&d_area, 4 * T, "area")) ||
+        (rc = alloc_into(&d_dist, 4 * T, "dist")) || (rc = alloc_into(&h->vol, T, "vol")) ||
+        (rc = alloc_into(&h->src, T, "src")) || (rc = alloc_into(&h->g, 4 * T, "g")) ||
+        (rc = alloc_into(&h->G, T, "G")) || (rc = alloc_into(&h->gmax, 1, "gmax")) ||
+        (rc = alloc_into(&h->err, 1, "err")))
+        return cleanup(rc);
+    cudaStream_t st = h->stream;
+    cudaError_t ce = cudaSuccess;
+    ce = ce ? ce : cudaMemcpyAsync(d_adj, adj, 16 * T, cudaMemcpyHostToDevice, st);
+    ce = ce ? ce : cudaMemcpyAsync(h->vol, vol, 8 * T, cudaMemcpyHostToDevice, st);
+    ce = ce ? ce : cudaMemcpyAsync(d_area, face_area, 32 * T, cudaMemcpyHostToDevice, st);
+    ce = ce ? ce : cudaMemcpyAsync(d_dist, centroid_dist, 32 * T, cudaMemcpyHostToDevice, st);
+    ce = ce ? ce : cudaMemsetAsync(h->gmax, 0, sizeof(unsigned long long), st);
+    ce = ce ? ce : cudaMemsetAsync(h->err, 0, sizeof(uint32_t), st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(RDSPLIT_ECUDA, "rdsplit_mesh_create: copy failed: %s", cudaGetErrorString(ce)));
+    }
+    launch_mesh_setup(n_tets, d_adj, h->vol, d_area, d_dist, h->src, h->g, h->G, h->gmax, h->err, st);
+    if ((rc = launch_check("rdsplit_mesh_create"))) return cleanup(rc);
+    if ((rc = check_err(h, "rdsplit_mesh_create"))) return cleanup(rc);
+    *out = h;
+    return cleanup(RDSPLIT_OK);
+}
+
+int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, const int32_t* lhs,
+                      const int32_t* rhs, const double* k, const uint8_t* mask, double tau_scale) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_model: NULL handle");
+    if (S < 1 || S > RDSPLIT_MAX_SPECIES)
+        return fail(RDSPLIT_EINVAL, "rdsplit_set_model: n_species must be in 1..%d", RDSPLIT_MAX_SPECIES);
+    if (R < 0 || R > RDSPLIT_MAX_REACTIONS)
+        return fail(RDSPLIT_EINVAL, "rdsplit_set_model: n_reactions must be in 0..%d", RDSPLIT_MAX_REACTIONS);
+    if (!D) return fail(RDSPLIT_EINVAL, "rdsplit_set_model: D is NULL");
+    if (R > 0 && (!lhs || !rhs || !k)) return fail(RDSPLIT_EINVAL, "rdsplit_set_model: reaction arrays NULL");
+    if (!(tau_scale > 0.0) || !(tau_scale <= 1.0))
+        return fail(RDSPLIT_EINVAL, "rdsplit_set_model: tau_scale must be in (0, 1]");
+    ModelParams mp{};
+    mp.S = S;
+    mp.R = R;
+    for (int s = 0; s < S; ++s) {
+        if (!(D[s] >= 0.0) || !std::isfinite(D[s]))
+            return fail(RDSPLIT_EINVAL, "rdsplit_set_model: D[%d] must be finite and >= 0", s);
+        mp.D[s] = D[s];
+    }
+    for (int r = 0; r < R; ++r) {
+        if (!(k[r] >= 0.0) || !std::isfinite(k[r]))
+            return fail(RDSPLIT_EINVAL, "rdsplit_set_model: k[%d] must be finite and >= 0", r);
+        mp.k[r] = k[r];
+        int order = 0;
+        for (int s = 0; s < S; ++s) {
+            int a = lhs[r * S + s], b = rhs[r * S + s];
+            if (a < 0 || b < 0 || a > 2 || b > 100)
+                return fail(RDSPLIT_EINVAL, "rdsplit_set_model: bad stoichiometry in reaction %d", r);
+            order += a;
+            mp.lhs[r][s] = (int8_t)a;
+            mp.delta[r][s] = (int8_t)(b - a);
+        }
+        if (order > 2) return fail(RDSPLIT_EINVAL, "rdsplit_set_model: reaction %d has order %d > 2", r, order);
+        mp.order[r] = (int8_t)order;
+    }
+    mp.any_reaction = R > 0 ? 1 : 0;
+    mp.has_mask = mask ? 1 : 0;
+
+    h->free_model();
+    const size_t T = (size_t)h->T;
+    int rc;
+    if ((rc = alloc_into(&h->D, (size_t)S, "D")) || (rc = alloc_into(&h->d_tau, 1, "tau")) ||
+        (rc = alloc_into(&h->cnt, T * S, "counts")) || (rc = alloc_into(&h->rem, T * S, "remainders")) ||
+        (rc = alloc_into(&h->out[0], T * S, "out-slots")) || (rc = alloc_into(&h->out[1], T * S, "out-slots")) ||
+        (rc = alloc_into(&h->thr, T * S, "thresholds")) || (rc = alloc_into(&h->thr_last, T * S, "thresholds")) ||
+        (rc = alloc_into(&h->staging, T * S, "staging"))) {
+        h->free_model();
+        return rc;
+    }
+    cudaStream_t st = h->stream;
+    if (mask) {
+        uint8_t* d_m8 = nullptr;
+        if ((rc = alloc_into(&d_m8, (size_t)R * T, "mask")) || (rc = alloc_into(&h->mask, T, "mask bits"))) {
+            dev_free(d_m8);
+            h->free_model();
+            return rc;
+        }
+        cudaError_t ce = cudaMemcpyAsync(d_m8, mask, (size_t)R * T, cudaMemcpyHostToDevice, st);
+        if (ce == cudaSuccess) launch_pack_mask(h->T, R, d_m8, h->mask, st);
+        cudaError_t ce2 = cudaStreamSynchronize(st);
+        dev_free(d_m8);
+        if (ce != cudaSuccess || ce2 != cudaSuccess) {
+            cudaGetLastError();
+            h->free_model();
+            return fail(RDSPLIT_ECUDA, "rdsplit_set_model: mask upload failed");
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->D, mp.D, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    launch_tau(h->D, S, h->gmax, tau_scale, h->d_tau, st);
+    CUDA_TRY(cudaMemcpyAsync(&h->tau, h->d_tau, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemsetAsync(h->cnt, 0, T * S * sizeof(int32_t), st));
+    CUDA_TRY(cudaMemsetAsync(h->rem, 0, T * S * sizeof(int32_t), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (std::isfinite(h->tau)) launch_thresholds(h->T, mp, h->g, h->G, h->tau, h->thr, st);
+    if ((rc = launch_check("rdsplit_set_model"))) return rc;
+    h->mp = mp;
+    h->S = S;
+    h->R = R;
+    h->has_model = true;
+    h->t = 0.0;
+    h->period = 0;
+    return check_err(h, "rdsplit_set_model");
+}
+
+static int set_counts_impl(rdsplit_mesh_t h, const int32_t* counts, bool device) {
+    if (!h || !counts) return fail(RDSPLIT_EINVAL, "rdsplit_set_counts: NULL argument");
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "rdsplit_set_counts: no model attached");
+    const size_t n = (size_t)h->T * h->S;
+    const int32_t* srcp = counts;
+    if (!device) {
+        CUDA_TRY(cudaMemcpyAsync(h->staging, counts, n * 4, cudaMemcpyHostToDevice, h->stream));
+        srcp = h->staging;
+    }
+    launch_counts_in(h->T, h->S, srcp, h->cnt, h->err, h->stream);
+    int rc = launch_check("rdsplit_set_counts");
+    if (rc) return rc;
+    return check_err(h, "rdsplit_set_counts");
+}
+
+int rdsplit_set_counts(rdsplit_mesh_t h, const int32_t* counts) { return set_counts_impl(h, counts, false); }
+int rdsplit_set_counts_device(rdsplit_mesh_t h, const int32_t* d) { return set_counts_impl(h, d, true); }
+
+static int get_counts_impl(rdsplit_mesh_t h, int32_t* out, bool device) {
+    if (!h || !out) return fail(RDSPLIT_EINVAL, "rdsplit_get_counts: NULL argument");
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "rdsplit_get_counts: no model attached");
+    const size_t n = (size_t)h->T * h->S;
+    int32_t* dst = device ? out : h->staging;
+    launch_counts_out(h->T, h->S, h->cnt, dst, h->stream);
+    int rc = launch_check("rdsplit_get_counts");
+    if (rc) return rc;
+    if (!device) CUDA_TRY(cudaMemcpyAsync(out, h->staging, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return RDSPLIT_OK;
+}
+
+int rdsplit_get_counts(rdsplit_mesh_t h, int32_t* out) { return get_counts_impl(h, out, false); }
+int rdsplit_get_counts_device(rdsplit_mesh_t h, int32_t* d) { return get_counts_impl(h, d, true); }
+
+int rdsplit_run(rdsplit_mesh_t h, double t_end, uint64_t seed) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_run: NULL handle");
+    return run_loop(h, t_end, -1, seed);
+}
+
+int rdsplit_run_periods(rdsplit_mesh_t h, int64_t n_periods, uint64_t seed) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_run_periods: NULL handle");
+    if (n_periods < 0) return fail(RDSPLIT_EINVAL, "rdsplit_run_periods: n_periods < 0");
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "rdsplit_run_periods: no model attached");
+    if (!std::isfinite(h->tau)) return fail(RDSPLIT_EINVAL, "rdsplit_run_periods: no species diffuses");
+    return run_loop(h, HUGE_VAL, n_periods, seed);
+}
+
+int rdsplit_get_time(rdsplit_mesh_t h, double* t, int64_t* period) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_get_time: NULL handle");
+    if (t) *t = h->t;
+    if (period) *period = h->period;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_set_time(rdsplit_mesh_t h, double t, int64_t period) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_time: NULL handle");
+    if (!std::isfinite(t) || period < 0) return fail(RDSPLIT_EINVAL, "rdsplit_set_time: bad time or period");
+    h->t = t;
+    h->period = period;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_get_tau(rdsplit_mesh_t h, double* tau) {
+    if (!h || !tau) return fail(RDSPLIT_EINVAL, "rdsplit_get_tau: NULL argument");
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "rdsplit_get_tau: no model attached");
+    *tau = h->tau;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_get_shape(rdsplit_mesh_t h, int32_t* n_tets, int32_t* n_species) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_get_shape: NULL handle");
+    if (n_tets) *n_tets = h->T;
+    if (n_species) *n_species = h->S;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_set_stream(rdsplit_mesh_t h, void* stream) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_stream: NULL handle");
+    h->stream = (cudaStream_t)stream;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_mesh_destroy(rdsplit_mesh_t h) {
+    if (!h) return RDSPLIT_OK;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+    return RDSPLIT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal interface between the host library (rd_api.cu) and the kernels
+// (rd_kernels.cu).  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rdk {
+
+constexpr int kMaxS = 16;   // species
+constexpr int kMaxR = 32;   // reactions (mask bits fit a uint32)
+
+// Error bits raised by kernels into a device word.
+enum : uint32_t {
+    kErrAdjRange = 1u << 0,      // neighbour index out of range or self
+    kErrAdjAsym = 1u << 1,       // adjacency not symmetric / duplicated
+    kErrVolume = 1u << 2,        // volume not finite and positive
+    kErrFace = 1u << 3,          // area or centroid distance invalid
+    kErrNegative = 1u << 4,      // negative count (input or invariant)
+    kErrOverflow = 1u << 5,      // a count would exceed INT32_MAX
+    kErrEventCap = 1u << 6,      // more SSA events in one tet-period than the cap
+    kErrTimeout = 1u << 7,       // a bounded device wait expired
+};
+
+// Chemistry, passed by value to kernels (lives in the constant bank).
+struct ModelParams {
+    int32_t S, R;
+    int32_t has_mask;
+    int32_t any_reaction;
+    double D[kMaxS];
+    double k[kMaxR];
+    int8_t lhs[kMaxR][kMaxS];
+    int8_t delta[kMaxR][kMaxS];   // rhs - lhs
+    int8_t order[kMaxR];
+};
+
+// Device arrays of one mesh + state.  Counts are species-major ([S][T]);
+// out-slots are [S][T][4]; src[t][f] = 4*adj[t][f] + (slot of t in that
+// neighbour) or -1.
+struct DevMesh {
+    int32_t T;
+    const int4* src;        // [T]
+    const double* g;        // [T][4] face coefficient A/(V dist)
+    const double* G;        // [T]   sum of g
+    const double* vol;      // [T]
+    const uint32_t* mask;   // [T]   reaction-on bits, or null
+};
+
+struct DevState {
+    int32_t* cnt;           // [S][T] counts between runs
+    int32_t* rem;           // [S][T] molecules that stayed in the last period
+    uint32_t* err;          // error word
+};
+
+// ---- setup --------------------------------------------------------------
+void launch_mesh_setup(int32_t T, const int32_t* adj, const double* vol, const double* area,
+                       const double* dist, int4* src, double* g, double* G,
+                       unsigned long long* gmax_bits, uint32_t* err, cudaStream_t st);
+void launch_tau(const double* D, int32_t S, const unsigned long long* gmax_bits, double tau_scale,
+                double* tau_out, cudaStream_t st);
+void launch_thresholds(int32_t T, const ModelParams& mp, const double* g, const double* G, double tau_k,
+                       uint4* thr, cudaStream_t st);
+void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, cudaStream_t st);
+void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* st_major, uint32_t* err,
+                      cudaStream_t st);
+void launch_counts_out(int32_t T, int32_t S, const int32_t* st_major, int32_t* ts, cudaStream_t st);
+
+// ---- one period (gather of the previous period fused with reactions and
+// diffusion of this one) and the closing gather --------------------------
+struct PeriodArgs {
+    uint32_t period;        // global period index (random-stream key)
+    double tau_k;           // length of this period
+    uint64_t seed;
+    int32_t first;          // 1: counts come from cnt (no pending transfer)
+    const uint4* thr;       // [S][T] cumulative 32-bit face thresholds for tau_k
+    const int4* out_prev;   // [S][T] out-slots of the previous period
+    int4* out_cur;          // [S][T] out-slots written by this period
+};
+void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+                   cudaStream_t st);
+void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int4* out_last, cudaStream_t st);
+
+int64_t launches();
+
+}  // namespace rdk

@@ -1,0 +1,379 @@
+// Kernels of the operator-splitting hot path (Algorithm 1 of
+// arXiv:1512.03126) for sm_103a.
+//
+//   k_mesh_setup   face coefficients g = A/(V dist), G = sum g, reverse-face
+//                  table, mesh validation, max G           (setup, Sec. II.A)
+//   k_tau          tau = tau_scale / max_s(D_s * max_t G_t) (Algorithm 1, precompute)
+//   k_thresholds   cumulative 32-bit face thresholds of zeta * w_f
+//   k_period       per tet: gather of the previous period's transfers, SSA
+//                  reactions with occupancy (Step 2), mean-corrected binomial
+//                  count and multinomial split (Step 3)
+//   k_gather       the closing synchronous transfer of a run
+//
+// Layout: counts and remainders are species-major int32 [S][T] (coalesced);
+// out-slots are int4 [S][T] (one 16-byte store per tet and species, the four
+// faces of a tet in one sector so that neighbours reading them share it).
+#include <atomic>
+#include <cmath>
+
+#include "rd_device.cuh"
+#include "rd_internal.h"
+
+namespace rdk {
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+constexpr int kBlock = 256;
+constexpr int kEventCap = 1 << 22;   // SSA events per tet and period
+constexpr double kAvogadro = 6.02214076e23;
+
+inline int grid_for(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+}  // namespace
+
+int64_t launches() { return g_launches.load(); }
+
+// ---------------------------------------------------------------- setup ----
+__global__ void k_mesh_setup(int32_t T, const int32_t* __restrict__ adj, const double* __restrict__ vol,
+                             const double* __restrict__ area, const double* __restrict__ dist,
+                             int4* __restrict__ src, double* __restrict__ g, double* __restrict__ G,
+                             unsigned long long* gmax_bits, uint32_t* err) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    uint32_t e = 0;
+    double V = vol[t];
+    if (!(V > 0.0) || !(V < HUGE_VAL)) e |= kErrVolume;
+    int s4[4];
+    double gf[4];
+    double Gt = 0.0;
+    for (int f = 0; f < 4; ++f) {
+        int u = adj[4 * t + f];
+        s4[f] = -1;
+        gf[f] = 0.0;
+        if (u >= 0) {
+            if (u >= T || u == t) {
+                e |= kErrAdjRange;
+            } else {
+                int slot = -1, hits = 0;
+                for (int r = 0; r < 4; ++r)
+                    if (adj[4 * u + r] == t) { slot = r; ++hits; }
+                if (hits != 1) e |= kErrAdjAsym;
+                else s4[f] = 4 * u + slot;
+                double A = area[4 * t + f], d = dist[4 * t + f];
+                if (!(A >= 0.0) || !(A < HUGE_VAL) || !(d > 0.0) || !(d < HUGE_VAL)) e |= kErrFace;
+                else gf[f] = A / (V * d);
+            }
+        } else if (u != -1) {
+            e |= kErrAdjRange;
+        }
+        Gt = Gt + gf[f];
+    }
+    src[t] = make_int4(s4[0], s4[1], s4[2], s4[3]);
+    for (int f = 0; f < 4; ++f) g[4 * t + f] = gf[f];
+    G[t] = Gt;
+    if (e) atomicOr(err, e);
+    else if (Gt < HUGE_VAL) atomicMax(gmax_bits, (unsigned long long)__double_as_longlong(Gt));
+}
+
+void launch_mesh_setup(int32_t T, const int32_t* adj, const double* vol, const double* area,
+                       const double* dist, int4* src, double* g, double* G,
+                       unsigned long long* gmax_bits, uint32_t* err, cudaStream_t st) {
+    k_mesh_setup<<<grid_for(T), kBlock, 0, st>>>(T, adj, vol, area, dist, src, g, G, gmax_bits, err);
+    ++g_launches;
+}
+
+// Rounding is monotone, so max_{s,t} fl(D_s G_t) = max_s fl(D_s max_t G_t).
+__global__ void k_tau(const double* D, int32_t S, const unsigned long long* gmax_bits, double tau_scale,
+                      double* tau_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double Gmax = __longlong_as_double((long long)*gmax_bits);
+    double dmax = 0.0;
+    for (int s = 0; s < S; ++s) {
+        double d = D[s] * Gmax;
+        if (d > dmax) dmax = d;
+    }
+    *tau_out = dmax > 0.0 ? tau_scale / dmax : __longlong_as_double(0x7ff0000000000000ll);
+}
+
+void launch_tau(const double* D, int32_t S, const unsigned long long* gmax_bits, double tau_scale,
+                double* tau_out, cudaStream_t st) {
+    k_tau<<<1, 32, 0, st>>>(D, S, gmax_bits, tau_scale, tau_out);
+    ++g_launches;
+}
+
+// Transfer probability over a period of length tau_k (Eq. 1 and the text
+// after it): zeta = tau_k * D * G, at most 1.
+__device__ __forceinline__ double zeta_of(double tau_k, double D, double Gt) {
+    double z = tau_k * (D * Gt);
+    return z > 1.0 ? 1.0 : z;
+}
+
+// C_f = floor(2^32 zeta (g_0 + ... + g_f) / G): a molecule leaves through the
+// first face f whose threshold exceeds its 32-bit draw, and stays if none does.
+__global__ void k_thresholds(int32_t T, ModelParams mp, const double* __restrict__ g,
+                             const double* __restrict__ G, double tau_k, uint4* __restrict__ thr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * mp.S) return;
+    int s = (int)(i / T);
+    int t = (int)(i - (int64_t)s * T);
+    double Gt = G[t];
+    double z = zeta_of(tau_k, mp.D[s], Gt);
+    uint32_t C[4] = {0, 0, 0, 0};
+    if (z > 0.0) {
+        double cum = 0.0;
+        for (int f = 0; f < 4; ++f) {
+            cum = cum + g[4 * t + f];
+            C[f] = rdd::threshold_of(z * (cum / Gt));
+        }
+    }
+    thr[i] = make_uint4(C[0], C[1], C[2], C[3]);
+}
+
+void launch_thresholds(int32_t T, const ModelParams& mp, const double* g, const double* G, double tau_k,
+                       uint4* thr, cudaStream_t st) {
+    k_thresholds<<<grid_for((int64_t)T * mp.S), kBlock, 0, st>>>(T, mp, g, G, tau_k, thr);
+    ++g_launches;
+}
+
+__global__ void k_pack_mask(int32_t T, int32_t R, const uint8_t* __restrict__ m8, uint32_t* __restrict__ m32) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    uint32_t bits = 0;
+    for (int r = 0; r < R; ++r)
+        if (m8[(size_t)r * T + t]) bits |= 1u << r;
+    m32[t] = bits;
+}
+
+void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, cudaStream_t st) {
+    k_pack_mask<<<grid_for(T), kBlock, 0, st>>>(T, R, mask8, mask32);
+    ++g_launches;
+}
+
+__global__ void k_counts_in(int32_t T, int32_t S, const int32_t* __restrict__ ts, int32_t* __restrict__ sm,
+                            uint32_t* err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * S) return;
+    int t = (int)(i / S), s = (int)(i - (int64_t)t * S);
+    int32_t v = ts[i];
+    if (v < 0) { atomicOr(err, kErrNegative); v = 0; }
+    sm[(int64_t)s * T + t] = v;
+}
+
+__global__ void k_counts_out(int32_t T, int32_t S, const int32_t* __restrict__ sm, int32_t* __restrict__ ts) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * S) return;
+    int t = (int)(i / S), s = (int)(i - (int64_t)t * S);
+    ts[i] = sm[(int64_t)s * T + t];
+}
+
+void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* sm, uint32_t* err, cudaStream_t st) {
+    k_counts_in<<<grid_for((int64_t)T * S), kBlock, 0, st>>>(T, S, ts, sm, err);
+    ++g_launches;
+}
+
+void launch_counts_out(int32_t T, int32_t S, const int32_t* sm, int32_t* ts, cudaStream_t st) {
+    k_counts_out<<<grid_for((int64_t)T * S), kBlock, 0, st>>>(T, S, sm, ts);
+    ++g_launches;
+}
+
+// ---------------------------------------------------------------- period ---
+// Incoming molecules of species s for tet t: what each neighbour sent through
+// the shared face in the previous period.
+__device__ __forceinline__ int64_t incoming(const int32_t* __restrict__ op, int4 sr) {
+    int64_t n = 0;
+    if (sr.x >= 0) n += __ldg(op + sr.x);
+    if (sr.y >= 0) n += __ldg(op + sr.y);
+    if (sr.z >= 0) n += __ldg(op + sr.z);
+    if (sr.w >= 0) n += __ldg(op + sr.w);
+    return n;
+}
+
+// Reaction phase of one tet (Algorithm 1, Step 2 and 2.1): Gillespie's
+// direct method over [0, tau_k); the first event at or past tau_k is
+// discarded.  Before a species' count changes, its occupancy integral
+// advances by N * (t_event - t_last).
+__device__ __forceinline__ void react_tet(const DevMesh& m, const ModelParams& mp, int t, uint32_t period,
+                                          double tau_k, uint64_t seed, int64_t* N, double* occ, double* tl,
+                                          uint32_t& touched, uint32_t* err) {
+    double avv = kAvogadro * (m.vol[t] * 1000.0);
+    uint32_t on = mp.has_mask ? m.mask[t] : 0xffffffffu;
+    rdd::Stream st(seed, (uint32_t)t, period, rdd::kPurposeReaction, 0);
+    double tc = 0.0;
+    int events = 0;
+    for (;;) {
+        double a[kMaxR];
+        double a0 = 0.0;
+        for (int r = 0; r < mp.R; ++r) {
+            double ar = 0.0;
+            if ((on >> r) & 1u) {
+                int64_t h = 1;
+                for (int s = 0; s < mp.S; ++s) {
+                    int nu = mp.lhs[r][s];
+                    if (nu == 1) h = h * N[s];
+                    else if (nu == 2) h = h * (N[s] * (N[s] - 1) / 2);
+                }
+                if (h != 0) {
+                    double kr = mp.k[r];
+                    int o = mp.order[r];
+                    double c = o == 0 ? kr * avv : (o == 1 ? kr : kr / avv);
+                    ar = c * (double)h;
+                }
+            }
+            a[r] = ar;
+            a0 = a0 + ar;
+        }
+        if (!(a0 > 0.0)) break;
+        double u1 = st.u01_open0();
+        double tn = tc + (-rdd::own_log(u1)) / a0;
+        if (tn >= tau_k) break;
+        double target = st.u01() * a0;
+        int mu = -1;
+        double cum = 0.0;
+        for (int r = 0; r < mp.R; ++r) {
+            cum = cum + a[r];
+            if (target < cum) { mu = r; break; }
+        }
+        if (mu < 0)
+            for (int r = mp.R - 1; r >= 0; --r)
+                if (a[r] > 0.0) { mu = r; break; }
+        for (int s = 0; s < mp.S; ++s) {
+            int dn = mp.delta[mu][s];
+            if (dn != 0) {
+                occ[s] = occ[s] + (double)N[s] * (tn - tl[s]);
+                tl[s] = tn;
+                touched |= 1u << s;
+                N[s] += dn;
+            }
+        }
+        tc = tn;
+        if (++events >= kEventCap) { atomicOr(err, kErrEventCap); break; }
+    }
+    for (int s = 0; s < mp.S; ++s)
+        if ((touched >> s) & 1u) occ[s] = occ[s] + (double)N[s] * (tau_k - tl[s]);
+}
+
+// Diffusion of one species out of one tet (Algorithm 1, Step 3; Eq. 2-3;
+// Sec. II.B): N* from the occupancy (stochastic rounding of N-bar when the
+// count changed during the period, else N), n = min(Binomial(N*, zeta), N),
+// split over the faces by conditional binomials; below N* = 10 the same law
+// one molecule at a time against the cumulative thresholds.
+__device__ __forceinline__ int4 diffuse(const DevMesh& m, int t, int s, double Dsp, uint32_t period, double tau_k,
+                                        uint64_t seed, int64_t Nt, bool touched, double occ, uint4 C) {
+    int4 o = make_int4(0, 0, 0, 0);
+    double Gt = m.G[t];
+    double z = zeta_of(tau_k, Dsp, Gt);
+    if (!(z > 0.0) || Nt <= 0) return o;
+    int64_t Nstar = Nt;
+    if (touched) {
+        rdd::Stream rs(seed, (uint32_t)t, period, rdd::kPurposeRounding, (uint32_t)s);
+        double nbar = occ / tau_k;
+        double fl = floor(nbar);
+        double frac = nbar - fl;
+        Nstar = (int64_t)fl + (rs.u01() < frac ? 1 : 0);
+    }
+    if (Nstar <= 0) return o;
+    rdd::Stream ds(seed, (uint32_t)t, period, rdd::kPurposeDiffusion, (uint32_t)s);
+    if (Nstar < 10) {
+        int64_t moved = 0;
+        for (int64_t i = 0; i < Nstar; ++i) {
+            if (moved == Nt) break;
+            uint32_t u = ds.u32();
+            if (rdd::below(u, C.x)) { o.x += 1; ++moved; }
+            else if (rdd::below(u, C.y)) { o.y += 1; ++moved; }
+            else if (rdd::below(u, C.z)) { o.z += 1; ++moved; }
+            else if (rdd::below(u, C.w)) { o.w += 1; ++moved; }
+        }
+        return o;
+    }
+    int64_t n = rdd::binomial(Nstar, z, ds);
+    if (n > Nt) n = Nt;
+    if (n == 0) return o;
+    double g[4];
+    for (int f = 0; f < 4; ++f) g[f] = m.g[4 * t + f];
+    double suf[4];
+    double acc = 0.0;
+    for (int f = 3; f >= 0; --f) { acc = g[f] + acc; suf[f] = acc; }
+    int last = -1;
+    for (int f = 0; f < 4; ++f)
+        if (g[f] > 0.0) last = f;
+    int64_t rest = n;
+    int64_t nf[4] = {0, 0, 0, 0};
+    for (int f = 0; f < 4; ++f) {
+        if (!(g[f] > 0.0)) continue;
+        if (f == last) { nf[f] = rest; break; }
+        int64_t x = rdd::binomial(rest, g[f] / suf[f], ds);
+        nf[f] = x;
+        rest -= x;
+    }
+    o = make_int4((int)nf[0], (int)nf[1], (int)nf[2], (int)nf[3]);
+    return o;
+}
+
+template <bool kReact>
+__global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, DevState s, PeriodArgs a) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int T = m.T;
+    int4 sr = m.src[t];
+    int64_t N[kMaxS];
+    uint32_t bad = 0;
+    for (int sp = 0; sp < mp.S; ++sp) {
+        int64_t n;
+        if (a.first) {
+            n = s.cnt[(int64_t)sp * T + t];
+        } else {
+            n = s.rem[(int64_t)sp * T + t] +
+                incoming(reinterpret_cast<const int32_t*>(a.out_prev + (int64_t)sp * T), sr);
+        }
+        if (n > 2147483647) { bad |= kErrOverflow; n = 2147483647; }
+        if (n < 0) { bad |= kErrNegative; n = 0; }
+        N[sp] = n;
+    }
+    double occ[kMaxS], tl[kMaxS];
+    uint32_t touched = 0;
+    if (kReact) {
+        for (int sp = 0; sp < mp.S; ++sp) { occ[sp] = 0.0; tl[sp] = 0.0; }
+        react_tet(m, mp, t, a.period, a.tau_k, a.seed, N, occ, tl, touched, s.err);
+    }
+    for (int sp = 0; sp < mp.S; ++sp) {
+        int64_t Nt = N[sp];
+        if (Nt < 0) { bad |= kErrNegative; Nt = 0; }
+        uint4 C = a.thr[(int64_t)sp * T + t];
+        bool tch = kReact && ((touched >> sp) & 1u);
+        int4 o = diffuse(m, t, sp, mp.D[sp], a.period, a.tau_k, a.seed, Nt, tch, kReact ? occ[sp] : 0.0, C);
+        a.out_cur[(int64_t)sp * T + t] = o;
+        int64_t r = Nt - ((int64_t)o.x + o.y + o.z + o.w);
+        if (r > 2147483647) { bad |= kErrOverflow; r = 2147483647; }
+        s.rem[(int64_t)sp * T + t] = (int32_t)r;
+    }
+    if (bad) atomicOr(s.err, bad);
+}
+
+void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+                   cudaStream_t st) {
+    if (mp.any_reaction) k_period<true><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
+    else k_period<false><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
+    ++g_launches;
+}
+
+__global__ void k_gather(DevMesh m, int32_t S, DevState s, const int4* __restrict__ out_last) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int T = m.T;
+    int4 sr = m.src[t];
+    uint32_t bad = 0;
+    for (int sp = 0; sp < S; ++sp) {
+        int64_t n = s.rem[(int64_t)sp * T + t] +
+                    incoming(reinterpret_cast<const int32_t*>(out_last + (int64_t)sp * T), sr);
+        if (n > 2147483647) { bad |= kErrOverflow; n = 2147483647; }
+        if (n < 0) { bad |= kErrNegative; n = 0; }
+        s.cnt[(int64_t)sp * T + t] = (int32_t)n;
+    }
+    if (bad) atomicOr(s.err, bad);
+}
+
+void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int4* out_last, cudaStream_t st) {
+    k_gather<<<grid_for(m.T), kBlock, 0, st>>>(m, S, s, out_last);
+    ++g_launches;
+}
+
+}  // namespace rdk

@@ -132,17 +132,35 @@ def kuhn_box(nx: int, ny: int, nz: int, size=(1e-6, 1e-6, 1e-6),
         interior = ((gx > 0) & (gx < nx) & (gy > 0) & (gy < ny) & (gz > 0) & (gz < nz))
         d = rng.uniform(-jitter, jitter, size=(X.shape[0], 3)) * np.array([hx, hy, hz])
         X[interior] += d[interior]
-    P = X[verts]                                     # [T][4][3]
-    e1 = P[:, 1] - P[:, 0]
-    e2 = P[:, 2] - P[:, 0]
-    e3 = P[:, 3] - P[:, 0]
-    det = np.einsum("ij,ij->i", e1, np.cross(e2, e3))
-    if not (np.all(det > 0) or np.all(det < 0)):
-        # an inverted tet: the same permutation orientation must hold for all
-        sign = np.sign(det)
-        perm = np.tile(np.array([1, -1, -1, 1, 1, -1]), det.shape[0] // 6)
-        if not np.all(sign * perm == (sign * perm)[0]):
-            raise ValueError("jitter inverted a tetrahedron; lower the jitter")
+    # Unjittered Kuhn tets alternate orientation with the parity of their
+    # axis permutation; a jittered tet whose orientation flipped is inverted.
+    parity = np.tile(np.array([1.0, -1.0, -1.0, 1.0, 1.0, -1.0]), verts.shape[0] // 6)
+
+    def signed_volumes(Xv):
+        P = Xv[verts]
+        e1 = P[:, 1] - P[:, 0]
+        e2 = P[:, 2] - P[:, 0]
+        e3 = P[:, 3] - P[:, 0]
+        return np.einsum("ij,ij->i", e1, np.cross(e2, e3)), P
+
+    det, P = signed_volumes(X)
+    ref = np.sign(det[0] * parity[0])
+    if jitter > 0.0:
+        # Vertices of a tet the jitter would invert (or flatten below 5% of
+        # the unjittered volume) get their displacement halved, repeatedly.
+        base = hx * hy * hz
+        for _ in range(60):
+            bad = (det * parity * ref) < 0.05 * base
+            if not bad.any():
+                break
+            vb = np.unique(verts[bad].reshape(-1))
+            vb = vb[interior[vb]]
+            d[vb] *= 0.5
+            X = np.stack([gx * hx, gy * hy, gz * hz], axis=1).astype(np.float64)
+            X[interior] += d[interior]
+            det, P = signed_volumes(X)
+    if np.any(det * parity * ref <= 0):
+        raise ValueError("inverted tetrahedron in the mesh")
     vol = np.abs(det) / 6.0
     others = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
     F = P[:, others]                                 # [T][4][3][3]
@@ -353,17 +371,36 @@ def random_model(mesh: Mesh, S: int, rng: np.random.Generator) -> Model:
 
 @dataclass
 class Request:
+    """One serving request; ``workload()`` builds its mesh and model on demand."""
     rid: int
     arrival: float
-    workload: Workload
+    n: int
+    S: int
+    t_end: float
+    model_seed: int
+    h: float = 0.05e-6
+
+    def workload(self) -> Workload:
+        L = self.n * self.h
+        mesh = cube(self.n, L, 0.2, 5000 + self.rid)
+        rng = np.random.Generator(np.random.PCG64(self.model_seed))
+        model = random_model(mesh, self.S, rng)
+        free = molecules(1e-6, L ** 3)
+        counts = place_by_volume(mesh, [free] * self.S, 7000 + self.rid)
+        return Workload(f"request_{self.rid}_n{self.n}_S{self.S}", mesh, model, counts, self.t_end,
+                        100 + self.rid, {"n": self.n, "S": self.S, "h_m": self.h})
+
+    @property
+    def n_tets(self) -> int:
+        return 6 * self.n ** 3
 
 
 def serving_requests(n_requests: int, rate: float = 200.0, seed: int = 5,
                      n_lo: int = 6, n_hi: int = 60, tmin: float = 1e-3, tmax: float = 50e-3,
                      h: float = 0.05e-6) -> list:
-    """Poisson arrivals; each request a jittered n^3*6 cube with n log-uniform
-    in [n_lo, n_hi] and cell size ``h``, 1-8 species, random chemistry,
-    t_end uniform in [tmin, tmax]."""
+    """Poisson arrivals at ``rate``/s; each request a jittered n^3*6 cube with
+    n log-uniform in [n_lo, n_hi] and cell size ``h``, 1-8 species, random
+    chemistry (``random_model``), t_end uniform in [tmin, tmax]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
@@ -371,12 +408,6 @@ def serving_requests(n_requests: int, rate: float = 200.0, seed: int = 5,
         t += rng.exponential(1.0 / rate)
         n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
         S = int(rng.integers(1, 9))
-        L = n * h
-        mesh = cube(n, L, 0.2, 5000 + i)
-        model = random_model(mesh, S, rng)
-        free = molecules(1e-6, L ** 3)
-        counts = place_by_volume(mesh, [free] * S, 7000 + i)
         t_end = float(rng.uniform(tmin, tmax))
-        out.append(Request(i, t, Workload(f"request_{i}_n{n}_S{S}", mesh, model, counts,
-                                          t_end, 100 + i, {"n": n, "S": S})))
+        out.append(Request(i, t, n, S, t_end, 9000 + i, h))
     return out
