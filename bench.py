@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the operator-splitting hot path on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+One *step* advances the whole workload from its initial state to t_end
+(every period of Algorithm 1: reactions, mean-corrected diffusion count,
+multinomial split, synchronous transfer).  The metric is tet-period updates
+per second (one tet advanced through one period, all species).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
+the stream the library launches on; L2 is flushed (256 MiB write) between
+steps, outside the events; barrier + synchronize on both sides; the maximum
+over ranks is reported.  Under torchrun each rank runs its own replica of
+the workload (weak scaling, no collective on the data path).
+
+Printed: one JSON line (rank 0) with the metric, the roofline of the period
+kernel (algorithmic bytes per launch / CUDA-event duration of sampled
+launches), the SM clocks sampled during the timed region, an end-to-end
+figure through the C ABI with host buffers, and the serial oracle timed on a
+bounded sample on the host cores (``cpu_baseline``).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "tet-period updates/s"
+UNIT = "tet-period/s"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+# --------------------------------------------------------------- workloads --
+
+def make_workload(name: str):
+    from paper_1512_03126_gb300 import inputs as I
+    if name == "rd48k":
+        return I.config_reaction_diffusion_48k()
+    if name == "diffusion3072":
+        return I.config_diffusion_3072()
+    if name == "bar":
+        return I.config_bar()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes_per_tet_period(S: int, R: int, masked: bool) -> int:
+    """Bytes the fused period kernel must move per tet and period: the
+    reverse-face table (16 B) and, per species, the remaining count (read 4,
+    write 4), the four incoming out-slots (16), the four outgoing out-slots
+    (16) and the cumulative face thresholds (16); with reactions the tet
+    volume (8) and, with a reaction mask, its bits (4)."""
+    return 16 + 56 * S + (8 if R > 0 else 0) + (4 if masked else 0)
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_03126_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the period kernel from a committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(PROFILES, f"k_period_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"kernel_source_digest:\s*([0-9a-f]+)", text)
+    if not m or not d or d.group(1) != kernel_source_digest():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- ours ---
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1512_03126_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    build.build()
+    from paper_1512_03126_gb300 import rdsplit as rd
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload)
+    T, S, R = w.mesh.n_tets, w.model.n_species, w.model.n_reactions
+    stream = torch.cuda.current_stream()
+    sim = rd.Simulation(w.mesh, w.model, stream=stream)
+    seed = w.seed + 1000 * rank
+    d_init = torch.from_numpy(np.ascontiguousarray(w.counts)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        rd.rdsplit_set_counts_device(sim.h, d_init)
+        rd.rdsplit_set_time(sim.h, 0.0, 0)
+        sim.run(w.t_end, seed)
+
+    for _ in range(args.warmup):
+        step()
+    _, periods = sim.time
+    tau = sim.tau
+    units_per_step = T * periods
+
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = rd.rdsplit_kernel_launches()
+    rd.rdsplit_set_timing(sim.h, 16)
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = rd.rdsplit_kernel_launches() - launches0
+    kms, kn = rd.rdsplit_get_timing(sim.h)
+    rd.rdsplit_set_timing(sim.h, 0)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    seconds = total_ms / 1e3
+    value = units_per_step * args.steps * world / seconds
+
+    # roofline of the period kernel
+    bpt = algorithmic_bytes_per_tet_period(S, R, w.model.mask is not None)
+    per_launch_s = (kms / kn) / 1e3 if kn else float("nan")
+    achieved = bpt * T / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"kernel": "k_period", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+                "bytes_per_tet_period": bpt, "launch_us": round(per_launch_s * 1e6, 3),
+                "sampled_launches": kn, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(np.ascontiguousarray(w.counts)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        hin, hout = host_in.numpy(), host_out.numpy()
+        for _ in range(1):
+            rd.rdsplit_set_counts(sim.h, hin)
+            rd.rdsplit_set_time(sim.h, 0.0, 0)
+            sim.run(w.t_end, seed)
+            rd.rdsplit_get_counts(sim.h, hout)
+        e_ms = 0.0
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rd.rdsplit_set_counts(sim.h, hin)
+            rd.rdsplit_set_time(sim.h, 0.0, 0)
+            sim.run(w.t_end, seed)
+            rd.rdsplit_get_counts(sim.h, hout)
+            e1.record(stream)
+            e1.synchronize()
+            e_ms += e0.elapsed_time(e1)
+        e2e = {"value": units_per_step * n_e2e * world / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    sim.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32 counts, f64 rates",
+        "data": "synthetic (seeded Kuhn-cube mesh and placement)",
+        "config": {"workload": w.name, "n_tets": T, "species": S, "reactions": R, "t_end_s": w.t_end,
+                   "periods": periods, "tau_s": tau, "tet_periods_per_step": units_per_step,
+                   "l2": "flushed between steps (256 MiB write); the 10 MB state stays L2-resident "
+                         "across the periods of a step by design",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+
+
+def cpu_baseline(w, seconds: float):
+    """The serial oracle, as it stands, on the host: a bounded number of
+    periods of the same workload, scaled to tet-period updates/s."""
+    from oracle import oracle as O
+    O.lib()
+    t0 = time.perf_counter()
+    O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=5)
+    per_period = (time.perf_counter() - t0) / 5
+    n = max(5, int(seconds / max(per_period, 1e-6)))
+    t0 = time.perf_counter()
+    _, _, p = O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=n)
+    dt = time.perf_counter() - t0
+    return {"value": w.mesh.n_tets * p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {p} periods of {w.name} ({w.mesh.n_tets} tets), one host core, {dt:.1f} s"}
+
+
+# -------------------------------------------------------------- reference ---
+
+def run_reference(args, rank, world):
+    """The serial oracle timed on the host cores on a bounded sample of the
+    same workload per step (the paper's reference implementation is not
+    available; this is the CPU restatement of the method)."""
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    O.lib()
+    w = make_workload(args.workload)
+    periods_per_step = max(1, int(args.ref_periods))
+    for _ in range(args.warmup):
+        O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=periods_per_step)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(args.steps):
+        _, _, p = O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=periods_per_step)
+        done += p
+    dt = time.perf_counter() - t0
+    value = w.mesh.n_tets * done / dt
+    sample = f"first {periods_per_step} periods of {w.name} per step, one host core"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32 counts, f64 rates",
+            "data": "synthetic", "config": {"workload": w.name, "n_tets": w.mesh.n_tets,
+                                            "periods_per_step": periods_per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rd48k")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-periods", type=int, default=300)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        import torch
+        if world > 1:
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,16 @@ int rdsplit_set_allocator(rdsplit_alloc_fn alloc, rdsplit_free_fn free_fn, void*
 /* Number of kernels the library has launched on this process so far. */
 int64_t rdsplit_kernel_launches(void);
 
+/*
+ * Profiling hook (tracing, no counterpart in the paper): when stride > 0,
+ * every stride-th launch of the period kernel is bracketed by CUDA events on
+ * the handle's stream and its device duration accumulated; stride = 0 turns
+ * sampling off.  rdsplit_get_timing returns the summed milliseconds and the
+ * number of sampled launches since the last rdsplit_set_timing call.
+ */
+int rdsplit_set_timing(rdsplit_mesh_t mesh, int32_t stride);
+int rdsplit_get_timing(rdsplit_mesh_t mesh, double* total_ms, int64_t* n_sampled);
+
 #ifdef __cplusplus
 }
 #endif

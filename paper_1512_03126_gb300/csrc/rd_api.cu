@@ -92,6 +92,12 @@ struct rdsplit_mesh {
     int32_t* staging = nullptr;
     ModelParams mp{};
     bool has_model = false;
+    // sampled kernel timing
+    int32_t timing_stride = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    double timing_ms = 0.0;
+    int64_t timing_n = 0;
     double tau = 0.0;
     double t = 0.0;
     int64_t period = 0;
@@ -107,6 +113,7 @@ struct rdsplit_mesh {
         has_model = false;
     }
     ~rdsplit_mesh() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         free_model();
         void* ps[] = {src, g, G, vol, gmax, err};
         for (void* p : ps) dev_free(p);
@@ -139,6 +146,29 @@ int check_err(rdsplit_mesh* h, const char* where) {
     if (e & kErrTimeout) return fail(RDSPLIT_ETIMEOUT, "%s: bounded device wait expired", where);
     if (e & kErrNegative) return fail(RDSPLIT_EINVAL, "%s: negative count", where);
     return fail(RDSPLIT_ECUDA, "%s: device error bits 0x%x", where, e);
+}
+
+// Event pairs bracketing sampled period-kernel launches; collected after the
+// stream is synchronised at the end of a run.
+cudaEvent_t next_event(rdsplit_mesh* h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+void collect_timing(rdsplit_mesh* h) {
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) == cudaSuccess) {
+            h->timing_ms += ms;
+            h->timing_n += 1;
+        }
+    }
+    h->ev_used = 0;
+    cudaGetLastError();
 }
 
 int launch_check(const char* where) {
@@ -178,7 +208,14 @@ int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) 
         }
         int4* cur = h->out[j & 1];
         PeriodArgs a{(uint32_t)h->period, tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->timing_stride > 0 && j % h->timing_stride == 0) {
+            e0 = next_event(h);
+            e1 = next_event(h);
+        }
+        if (e0 && e1) cudaEventRecord(e0, h->stream);
         launch_period(m, h->mp, s, a, h->stream);
+        if (e0 && e1) cudaEventRecord(e1, h->stream);
         prev = cur;
         h->t = last ? t_end : h->t + h->tau;
         h->period += 1;
@@ -187,7 +224,9 @@ int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) 
     if (j > 0) launch_gather(m, h->S, s, prev, h->stream);
     int rc = launch_check("rdsplit_run");
     if (rc) return rc;
-    return check_err(h, "rdsplit_run");
+    rc = check_err(h, "rdsplit_run");
+    collect_timing(h);
+    return rc;
 }
 
 }  // namespace rdapi
@@ -415,6 +454,22 @@ int rdsplit_get_shape(rdsplit_mesh_t h, int32_t* n_tets, int32_t* n_species) {
 int rdsplit_set_stream(rdsplit_mesh_t h, void* stream) {
     if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_stream: NULL handle");
     h->stream = (cudaStream_t)stream;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_set_timing(rdsplit_mesh_t h, int32_t stride) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_timing: NULL handle");
+    if (stride < 0) return fail(RDSPLIT_EINVAL, "rdsplit_set_timing: stride < 0");
+    h->timing_stride = stride;
+    h->timing_ms = 0.0;
+    h->timing_n = 0;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_get_timing(rdsplit_mesh_t h, double* total_ms, int64_t* n) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_get_timing: NULL handle");
+    if (total_ms) *total_ms = h->timing_ms;
+    if (n) *n = h->timing_n;
     return RDSPLIT_OK;
 }
 

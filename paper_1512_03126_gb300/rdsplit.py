@@ -52,6 +52,8 @@ def _declare(L):
         "rdsplit_set_stream": ([vp, vp], C.c_int),
         "rdsplit_mesh_destroy": ([vp], C.c_int),
         "rdsplit_set_allocator": ([vp, vp, vp], C.c_int),
+        "rdsplit_set_timing": ([vp, i32], C.c_int),
+        "rdsplit_get_timing": ([vp, C.POINTER(dbl), C.POINTER(i64)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -184,6 +186,16 @@ def rdsplit_set_stream(h, stream):
 
 def rdsplit_mesh_destroy(h):
     _check(lib().rdsplit_mesh_destroy(h))
+
+
+def rdsplit_set_timing(h, stride: int):
+    _check(lib().rdsplit_set_timing(h, int(stride)))
+
+
+def rdsplit_get_timing(h):
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().rdsplit_get_timing(h, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
