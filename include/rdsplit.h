@@ -155,6 +155,49 @@ int64_t rdsplit_kernel_launches(void);
 int rdsplit_set_timing(rdsplit_mesh_t mesh, int32_t stride);
 int rdsplit_get_timing(rdsplit_mesh_t mesh, double* total_ms, int64_t* n_sampled);
 
+/*
+ * Allocation-free run (the paper has no counterpart; this is a deployment
+ * variant of rdsplit_run).  Some callers cannot call cudaMalloc: code running
+ * inside a host application that owns all device memory (a plugin with a
+ * fixed memory budget), or a real-time loop that must not stall on the
+ * device synchronisation an allocation can cause.  This entry point performs
+ * no device allocation or free of any kind: every intermediate array lives in
+ * one static device array of RDSPLIT_STATIC_SCRATCH_BYTES that the library
+ * reserves on each GPU that loads it, until the process exits.
+ *
+ * It runs Algorithm 1 exactly as rdsplit_run does (same kernels, same
+ * results) on caller-owned memory:
+ *   d_adj, d_vol, d_face_area, d_centroid_dist   the mesh, in DEVICE memory,
+ *                 same layout and rules as rdsplit_mesh_create
+ *   n_species, D, n_reactions, lhs, rhs, k      the model, in HOST memory,
+ *                 same rules as rdsplit_set_model
+ *   d_rxn_tet_mask   DEVICE uint8 [n_reactions][n_tets] or NULL
+ *   d_counts      DEVICE int32 [n_tets][n_species]; read at the start,
+ *                 overwritten with the counts at the end
+ *   t, period     HOST in/out: current time and global period index
+ *   t_end, seed   as for rdsplit_run
+ *   stream        cudaStream_t for all work (NULL: legacy default stream);
+ *                 the call synchronises it before returning
+ * Scratch needed: rdsplit_static_scratch_bytes(n_tets, n_species, masked);
+ * larger problems are rejected with RDSPLIT_EINVAL and a message giving
+ * both sizes.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any
+ * stream capture.  All calls share the one array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls whose
+ * device work overlaps, on any streams or threads, race on it and must be
+ * serialised by the caller.
+ */
+#define RDSPLIT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+size_t rdsplit_static_scratch_bytes(int32_t n_tets, int32_t n_species, int32_t masked);
+int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const double* d_vol,
+                       const double* d_face_area, const double* d_centroid_dist,
+                       int32_t n_species, const double* D, int32_t n_reactions,
+                       const int32_t* lhs, const int32_t* rhs, const double* k,
+                       const uint8_t* d_rxn_tet_mask, double tau_scale, int32_t* d_counts,
+                       double* t, int64_t* period, double t_end, uint64_t seed,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

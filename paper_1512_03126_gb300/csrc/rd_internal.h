@@ -80,5 +80,6 @@ void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, c
 void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int4* out_last, cudaStream_t st);
 
 int64_t launches();
+void note_launch();   // count a launch issued outside this file's launchers
 
 }  // namespace rdk

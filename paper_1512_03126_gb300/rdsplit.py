@@ -53,6 +53,9 @@ def _declare(L):
         "rdsplit_mesh_destroy": ([vp], C.c_int),
         "rdsplit_set_allocator": ([vp, vp, vp], C.c_int),
         "rdsplit_set_timing": ([vp, i32], C.c_int),
+        "rdsplit_static_scratch_bytes": ([i32, i32, i32], C.c_size_t),
+        "rdsplit_run_static": ([i32, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, dbl, vp,
+                                C.POINTER(dbl), C.POINTER(i64), dbl, u64, vp], C.c_int),
         "rdsplit_get_timing": ([vp, C.POINTER(dbl), C.POINTER(i64)], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -196,6 +199,34 @@ def rdsplit_get_timing(h):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().rdsplit_get_timing(h, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+RDSPLIT_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def rdsplit_static_scratch_bytes(n_tets: int, n_species: int, masked: bool = False) -> int:
+    return int(lib().rdsplit_static_scratch_bytes(int(n_tets), int(n_species), int(bool(masked))))
+
+
+def rdsplit_run_static(n_tets, d_adj, d_vol, d_face_area, d_centroid_dist, n_species, D, n_reactions,
+                       lhs, rhs, k, d_rxn_tet_mask, tau_scale, d_counts, t, period, t_end, seed,
+                       stream=None):
+    """Allocation-free run: mesh arrays, mask and counts are device tensors
+    (caller-owned); the model arrays are host arrays.  Returns (t, period)."""
+    R = int(n_reactions)
+    D = _c(D, np.float64, (n_species,))
+    lhs = _c(lhs, np.int32, (R, n_species)) if R else None
+    rhs = _c(rhs, np.int32, (R, n_species)) if R else None
+    k = _c(k, np.float64, (R,)) if R else None
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    tt, pp = C.c_double(t), C.c_int64(period)
+    _check(lib().rdsplit_run_static(int(n_tets), _ptr(d_adj), _ptr(d_vol), _ptr(d_face_area),
+                                    _ptr(d_centroid_dist), int(n_species), _ptr(D), R, _ptr(lhs), _ptr(rhs),
+                                    _ptr(k), _ptr(d_rxn_tet_mask), float(tau_scale), _ptr(d_counts),
+                                    C.byref(tt), C.byref(pp), float(t_end), int(seed),
+                                    C.c_void_p(stream or 0)))
+    return tt.value, pp.value
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
