@@ -46,6 +46,14 @@ PROFILES = os.path.join(ROOT, "profiles")
 
 # --------------------------------------------------------------- workloads --
 
+def engine_bytes_per_entry(S: int) -> int:
+    """Bytes the lockstep engine must move per processed (slot, tet) entry:
+    the list entry (8), the reverse-face table (16), one list append and its
+    flag (10) and, per species, the count read and clear (8), the thresholds
+    (16), the kept-count add (4) and the four face adds (16)."""
+    return 34 + 44 * S
+
+
 def make_workload(name: str):
     from paper_1512_03126_gb300 import inputs as I
     if name == "rd48k":
@@ -287,6 +295,178 @@ def cpu_baseline(w, seconds: float):
             "sample": f"first {p} periods of {w.name} ({w.mesh.n_tets} tets), one host core, {dt:.1f} s"}
 
 
+# ---------------------------------------------------------------- ensemble --
+
+def run_ensemble(args, rank, world, local_rank):
+    """512 independent simulations (n^3*6 jittered cubes, n ~ U{6..40}), each
+    run from its initial state to t_end = 0.1 s: batched in the lockstep
+    engine (one launch per global step for all of them) against the plain
+    form (each simulation's own launch sequence through rdsplit_run)."""
+    import torch
+    from paper_1512_03126_gb300 import build, inputs as I
+    build.build()
+    from paper_1512_03126_gb300 import rdsplit as rd
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    sizes = I.ensemble_sizes()
+    n_inst = len(sizes) if args.instances <= 0 else min(args.instances, len(sizes))
+    t0 = time.perf_counter()
+    ws = [I.ensemble_instance(i, int(sizes[i])) for i in range(n_inst)]
+    gen_s = time.perf_counter() - t0
+    seeds = [w.seed + 100000 * rank for w in ws]
+    sims = [rd.Simulation(w.mesh, w.model, stream=stream) for w in ws]
+    inits = [torch.from_numpy(np.ascontiguousarray(w.counts)).to(dev) for w in ws]
+    total_tets = sum(w.mesh.n_tets for w in ws)
+    periods = []
+    for w, s in zip(ws, sims):
+        tau = s.tau
+        t, P = 0.0, 0
+        while t < w.t_end:
+            t = w.t_end if t + tau > w.t_end else t + tau
+            P += 1
+        periods.append(P)
+    units = sum(w.mesh.n_tets * P for w, P in zip(ws, periods))
+    eng = rd.rdsplit_engine_create(n_inst, total_tets)
+    rd.rdsplit_engine_set_stream(eng, stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def reset():
+        for s, x in zip(sims, inits):
+            rd.rdsplit_set_counts_device(s.h, x)
+            rd.rdsplit_set_time(s.h, 0.0, 0)
+
+    def batched():
+        for s, w, sd in zip(sims, ws, seeds):
+            rd.rdsplit_engine_add(eng, s.h, w.t_end, sd)
+        rd.rdsplit_engine_step(eng, 1 << 40)
+        rd.rdsplit_engine_poll(eng, 1 << 16)
+
+    for _ in range(args.warmup):
+        reset()
+        batched()
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = rd.rdsplit_kernel_launches()
+    steps0, proc0, _, _ = rd.rdsplit_engine_stats(eng)
+    rd.rdsplit_engine_set_timing(eng, 1)
+    total_ms = 0.0
+    for _ in range(args.steps):
+        reset()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batched()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = rd.rdsplit_kernel_launches() - launches0
+    steps1, proc1, kms, kn = rd.rdsplit_engine_stats(eng)
+    rd.rdsplit_engine_set_timing(eng, 0)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = units * args.steps * world / (total_ms / 1e3)
+    gsteps = (steps1 - steps0) / args.steps
+    entries = (proc1 - proc0) / args.steps
+    bpe = engine_bytes_per_entry(1)
+    per_launch_s = (kms / kn) / 1e3 if kn else float("nan")
+    launches_per_step = kn / args.steps if args.steps else 1
+    achieved = bpe * (entries / launches_per_step) / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"kernel": "k_engine_step", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("ensemble"),
+                "bytes_per_entry": bpe, "entries_per_launch": round(entries / launches_per_step, 1),
+                "launch_us": round(per_launch_s * 1e6, 3), "sampled_launches": kn,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # the plain form: each simulation through its own rdsplit_run
+    plain = None
+    if rank == 0 and not args.no_plain:
+        reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s, w, sd in zip(sims, ws, seeds):
+            s.run(w.t_end, sd)
+        e1.record(stream)
+        e1.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": units / (pms / 1e3), "unit": UNIT, "ms": pms,
+                 "launches": sum(periods) + 2 * n_inst,
+                 "form": "one rdsplit_run launch sequence per simulation (dense period kernel)"}
+
+    # end to end: host counts in, host counts out, through the public calls
+    e2e = None
+    if not args.no_e2e:
+        host_in = [torch.from_numpy(np.ascontiguousarray(w.counts)).pin_memory() for w in ws]
+        host_out = [torch.empty_like(x).pin_memory() for x in host_in]
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s, x in zip(sims, host_in):
+            rd.rdsplit_set_counts(s.h, x.numpy())
+            rd.rdsplit_set_time(s.h, 0.0, 0)
+        rd.rdsplit_ensemble_run([s.h for s in sims], [w.t_end for w in ws], seeds)
+        for s, y in zip(sims, host_out):
+            rd.rdsplit_get_counts(s.h, y.numpy())
+        e1.record(stream)
+        e1.synchronize()
+        ems = e0.elapsed_time(e1)
+        nb = sum(int(x.numel()) * 4 for x in host_in)
+        e2e = {"value": units * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.lib()
+        t0 = time.perf_counter()
+        done, k = 0, 0
+        while time.perf_counter() - t0 < args.cpu_seconds and k < n_inst:
+            w = ws[k]
+            _, _, p = O.run(w.mesh, w.model, w.counts, w.t_end, seeds[k], max_periods=args.cpu_periods)
+            done += w.mesh.n_tets * p
+            k += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_periods} periods of instances 0..{k - 1} of the ensemble, "
+                         f"one host core, {dt:.1f} s"}
+
+    rd.rdsplit_engine_destroy(eng)
+    for s in sims:
+        s.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32 counts, f64 rates",
+        "data": "synthetic (seeded jittered Kuhn cubes, point-source initial state)",
+        "config": {"workload": f"batched ensemble of {n_inst} cubes n^3*6, n~U{{6..40}}, t_end 0.1 s",
+                   "instances": n_inst, "tets": total_tets, "tet_periods_per_step": units,
+                   "engine_periods_per_step": gsteps, "periods_sum": sum(periods), "periods_max": max(periods),
+                   "processed_entries_per_step": entries, "mesh_generation_s": round(gen_s, 1),
+                   "l2": "flushed between steps (256 MiB write); per step the ensemble state is 2.3 GB",
+                   "parallelism": f"replicas x{world} (each rank its own ensemble, own seeds)"},
+        "roofline": roofline, "plain": plain,
+        "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
+    }
+
+
 # -------------------------------------------------------------- reference ---
 
 def run_reference(args, rank, world):
@@ -297,23 +477,32 @@ def run_reference(args, rank, world):
         return None
     from oracle import oracle as O
     O.lib()
-    w = make_workload(args.workload)
     periods_per_step = max(1, int(args.ref_periods))
-    for _ in range(args.warmup):
-        O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=periods_per_step)
+    if args.workload == "ensemble":
+        from paper_1512_03126_gb300 import inputs as I
+        sizes = I.ensemble_sizes()
+        batch = [I.ensemble_instance(i, int(sizes[i])) for i in range(max(args.steps, 1))]
+        name = "batched ensemble (instance k at step k)"
+    else:
+        batch = [make_workload(args.workload)] * max(args.steps, 1)
+        name = batch[0].name
+    for k in range(args.warmup):
+        w = batch[k % len(batch)]
+        O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=min(periods_per_step, 20))
     t0 = time.perf_counter()
     done = 0
-    for _ in range(args.steps):
+    for k in range(args.steps):
+        w = batch[k]
         _, _, p = O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=periods_per_step)
-        done += p
+        done += w.mesh.n_tets * p
     dt = time.perf_counter() - t0
-    value = w.mesh.n_tets * done / dt
-    sample = f"first {periods_per_step} periods of {w.name} per step, one host core"
+    value = done / dt
+    sample = f"first {periods_per_step} periods of one simulation per step ({name}), one host core"
+    w = batch[0]
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32 counts, f64 rates",
-            "data": "synthetic", "config": {"workload": w.name, "n_tets": w.mesh.n_tets,
-                                            "periods_per_step": periods_per_step},
+            "data": "synthetic", "config": {"workload": name, "periods_per_step": periods_per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -324,11 +513,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="rd48k")
+    ap.add_argument("--workload", default="ensemble")
+    ap.add_argument("--instances", type=int, default=0, help="ensemble: use the first N instances (0 = all 512)")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-periods", type=int, default=300)
+    ap.add_argument("--cpu-periods", type=int, default=40)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -343,7 +535,7 @@ def main():
         if world > 1:
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        out = run_ours(args, rank, world, local_rank)
+        out = (run_ensemble if args.workload == "ensemble" else run_ours)(args, rank, world, local_rank)
         if world > 1:
             torch.distributed.destroy_process_group()
     if out is not None:

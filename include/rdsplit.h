@@ -156,6 +156,57 @@ int rdsplit_set_timing(rdsplit_mesh_t mesh, int32_t stride);
 int rdsplit_get_timing(rdsplit_mesh_t mesh, double* total_ms, int64_t* n_sampled);
 
 /*
+ * Batched engine: many independent simulations advanced by one persistent
+ * kernel in which each thread block takes one simulation from a queue
+ * (largest first) and runs its periods itself, touching only tets that hold
+ * molecules (or have a zero-order reaction switched on).  Realisations in
+ * parallel are the embarrassingly parallel use of Sec. I; each simulation's
+ * counts are exactly those rdsplit_run would give it alone (its random
+ * streams are keyed by its own seed, period index and canonical tet ids),
+ * whatever else runs beside it.
+ *
+ * rdsplit_engine_create: max_slots simultaneous simulations; max_active_tets
+ *   bounds the sum of n_tets over simulations in the engine (admission limit).
+ * rdsplit_engine_add: a mesh handle with its model and counts joins; it will
+ *   run from its current time to t_end with `seed` (as rdsplit_run would).
+ *   RDSPLIT_ENOMEM if no slot or capacity is free.  The handle must not be
+ *   used otherwise until it has finished.
+ * rdsplit_engine_step: advance every active simulation by up to n_steps
+ *   periods in one launch (a time slice); synchronises the engine's stream.
+ *   Finished handles hold their final counts, time and period index.
+ *   Between calls, simulations may be added (continuous batching).
+ * rdsplit_engine_poll: slot ids of simulations finished since the last poll.
+ * rdsplit_engine_active: number of active simulations and their total tets.
+ * rdsplit_ensemble_run: convenience — run n handles to t_end[i] with
+ *   seeds[i] in one engine (the batched ensemble, one launch).
+ * All device work is issued on the engine's stream (rdsplit_engine_set_stream;
+ * default: the legacy default stream); the meshes' own work must not overlap
+ * it.
+ */
+typedef struct rdsplit_engine* rdsplit_engine_t;
+int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_engine_t* out);
+int rdsplit_engine_set_stream(rdsplit_engine_t engine, void* stream);
+int rdsplit_engine_add(rdsplit_engine_t engine, rdsplit_mesh_t mesh, double t_end, uint64_t seed,
+                       int32_t* slot_out);
+int rdsplit_engine_step(rdsplit_engine_t engine, int64_t n_steps);
+int rdsplit_engine_poll(rdsplit_engine_t engine, int32_t* slots, int32_t max, int32_t* n_out);
+int rdsplit_engine_active(rdsplit_engine_t engine, int32_t* n_slots, int64_t* n_tets);
+int rdsplit_engine_destroy(rdsplit_engine_t engine);
+/* Scheduling: `in_flight` simulations are processed at once (0 = one per
+ * `cluster` SMs), each by a thread-block cluster of `cluster` CTAs (1, 2 or
+ * 4; default 4) that share its work through distributed shared memory.
+ * Fewer in flight keeps their working sets in L2. */
+int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
+/* Profiling: time every engine launch with CUDA events (on != 0), and read
+ * the periods advanced (maximum per step call, summed), the (simulation, tet)
+ * entries processed, and the summed milliseconds / number of timed launches. */
+int rdsplit_engine_set_timing(rdsplit_engine_t engine, int32_t on);
+int rdsplit_engine_stats(rdsplit_engine_t engine, int64_t* steps, int64_t* processed,
+                         double* timing_ms, int64_t* timing_n);
+int rdsplit_ensemble_run(int32_t n, const rdsplit_mesh_t* meshes, const double* t_end,
+                         const uint64_t* seeds);
+
+/*
  * Allocation-free run (the paper has no counterpart; this is a deployment
  * variant of rdsplit_run).  Some callers cannot call cudaMalloc: code running
  * inside a host application that owns all device memory (a plugin with a

@@ -249,6 +249,7 @@ int64_t binomial(int64_t n, double p, Stream& st) {
 
 // -------------------------------------------------------------- the model ---
 const double kAvogadro = 6.02214076e23;
+const int64_t kMoleculeCut = 4096;   // one draw per molecule below this N*
 const int kMaxSpecies = 16;
 const int kMaxReactions = 64;
 
@@ -392,10 +393,13 @@ void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t 
 //  3.3  n is split over the faces multinomially by conditional binomials in
 //       canonical face order, p_i = w_i / (w_i + ... + w_3), the last face
 //       with a neighbour taking the rest.
-//  Below N* = 10 (Sec. II.B) the same law is drawn one molecule at a time:
-//  each of N* molecules leaves through face f with probability zeta*w_f (as
-//  32-bit thresholds) and stays otherwise; draws stop once N(tau_k)
-//  molecules have left.
+//  Below N* = kMoleculeCut the same law is drawn one molecule at a time
+//  (Sec. II.B, "randomly selecting a direction for each molecule"): each of
+//  N* molecules leaves through face f with probability zeta*w_f (as 32-bit
+//  thresholds) and stays otherwise; draws stop once N(tau_k) molecules have
+//  left.  The paper switches at n = 10 for speed on a CPU; this build
+//  switches at 4096, where one draw per molecule spread over a warp is
+//  faster on the GPU than the double-precision samplers.
 void diffuse_tet_species(const Problem& P, const Geometry& geo, int t, int s, uint32_t period,
                          double tau_k, uint64_t seed, int64_t Nt, bool touched, double occ,
                          int64_t out[4]) {
@@ -414,7 +418,7 @@ void diffuse_tet_species(const Problem& P, const Geometry& geo, int t, int s, ui
     if (Nstar <= 0) return;
     const double* g = &geo.g[4 * t];
     Stream st(seed, (uint32_t)t, period, kDiffusion, (uint32_t)s);
-    if (Nstar < 10) {
+    if (Nstar < kMoleculeCut) {
         uint32_t C[4];
         double cum = 0.0;
         for (int f = 0; f < 4; ++f) {

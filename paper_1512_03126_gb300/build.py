@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librdsplit.so")
-SOURCES = ["rd_kernels.cu", "rd_api.cu", "rd_static.cu"]
+SOURCES = ["rd_kernels.cu", "rd_api.cu", "rd_static.cu", "rd_engine.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

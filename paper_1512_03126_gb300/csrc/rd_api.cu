@@ -70,56 +70,6 @@ using namespace rdapi;
         }                                                                                  \
     } while (0)
 
-struct rdsplit_mesh {
-    int32_t T = 0, S = 0, R = 0;
-    cudaStream_t stream = 0;
-    // geometry
-    int4* src = nullptr;
-    double* g = nullptr;
-    double* G = nullptr;
-    double* vol = nullptr;
-    uint32_t* mask = nullptr;
-    unsigned long long* gmax = nullptr;
-    uint32_t* err = nullptr;
-    // model and state
-    double* D = nullptr;
-    double* d_tau = nullptr;
-    int32_t* cnt = nullptr;
-    int32_t* rem = nullptr;
-    int4* out[2] = {nullptr, nullptr};
-    uint4* thr = nullptr;
-    uint4* thr_last = nullptr;
-    int32_t* staging = nullptr;
-    ModelParams mp{};
-    bool has_model = false;
-    // sampled kernel timing
-    int32_t timing_stride = 0;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    double timing_ms = 0.0;
-    int64_t timing_n = 0;
-    double tau = 0.0;
-    double t = 0.0;
-    int64_t period = 0;
-
-    DevMesh dev_mesh() const { return DevMesh{T, src, g, G, vol, mask}; }
-    DevState dev_state() const { return DevState{cnt, rem, err}; }
-
-    void free_model() {
-        void* ps[] = {D, d_tau, cnt, rem, out[0], out[1], thr, thr_last, staging, mask};
-        for (void* p : ps) dev_free(p);
-        D = nullptr; d_tau = nullptr; cnt = nullptr; rem = nullptr; out[0] = out[1] = nullptr;
-        thr = nullptr; thr_last = nullptr; staging = nullptr; mask = nullptr;
-        has_model = false;
-    }
-    ~rdsplit_mesh() {
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-        free_model();
-        void* ps[] = {src, g, G, vol, gmax, err};
-        for (void* p : ps) dev_free(p);
-    }
-};
-
 namespace {
 
 template <typename T>
@@ -130,7 +80,7 @@ int alloc_into(T** p, size_t count, const char* what) {
 }
 
 // Read and clear the device error word; translate kernel error bits.
-int check_err(rdsplit_mesh* h, const char* where) {
+int check_err_impl(rdsplit_mesh* h, const char* where) {
     uint32_t e = 0;
     CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -181,6 +131,8 @@ int launch_check(const char* where) {
 
 namespace rdapi {
 
+int check_err(rdsplit_mesh* h, const char* where) { return check_err_impl(h, where); }
+
 // The period loop of Algorithm 1 for one handle.  Step 1: the last period is
 // shortened so that it ends on t_end.  Step 2-3 run in k_period, which also
 // applies the previous period's transfers; the closing k_gather applies the
@@ -207,7 +159,7 @@ int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) 
             thr = h->thr_last;
         }
         int4* cur = h->out[j & 1];
-        PeriodArgs a{(uint32_t)h->period, tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
+        PeriodArgs a{(uint32_t)h->period, tau_k, (float)tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->timing_stride > 0 && j % h->timing_stride == 0) {
             e0 = next_event(h);
@@ -328,6 +280,7 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
     }
     mp.any_reaction = R > 0 ? 1 : 0;
     mp.has_mask = mask ? 1 : 0;
+    finish_model_params(mp);
 
     h->free_model();
     const size_t T = (size_t)h->T;
@@ -336,7 +289,7 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
         (rc = alloc_into(&h->cnt, T * S, "counts")) || (rc = alloc_into(&h->rem, T * S, "remainders")) ||
         (rc = alloc_into(&h->out[0], T * S, "out-slots")) || (rc = alloc_into(&h->out[1], T * S, "out-slots")) ||
         (rc = alloc_into(&h->thr, T * S, "thresholds")) || (rc = alloc_into(&h->thr_last, T * S, "thresholds")) ||
-        (rc = alloc_into(&h->staging, T * S, "staging"))) {
+        (rc = alloc_into(&h->staging, T * S, "staging")) || (rc = alloc_into(&h->avv, T, "avv"))) {
         h->free_model();
         return rc;
     }
@@ -359,6 +312,7 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
         }
     }
     CUDA_TRY(cudaMemcpyAsync(h->D, mp.D, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    launch_avv(h->T, h->vol, h->avv, st);
     launch_tau(h->D, S, h->gmax, tau_scale, h->d_tau, st);
     CUDA_TRY(cudaMemcpyAsync(&h->tau, h->d_tau, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemsetAsync(h->cnt, 0, T * S * sizeof(int32_t), st));

@@ -1,13 +1,74 @@
-// Host-side helpers shared by the C-ABI translation units.
+// Host-side helpers and the handle layout shared by the C-ABI translation units.
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
+#include "rd_internal.h"
 #include "rdsplit.h"
 
 namespace rdapi {
 int fail(int code, const char* fmt, ...);
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
+}  // namespace rdapi
+
+// One mesh + model + state on the device.
+struct rdsplit_mesh {
+    int32_t T = 0, S = 0, R = 0;
+    cudaStream_t stream = 0;
+    // geometry
+    int4* src = nullptr;
+    double* g = nullptr;
+    double* G = nullptr;
+    double* vol = nullptr;
+    uint32_t* mask = nullptr;
+    float2* avv = nullptr;
+    unsigned long long* gmax = nullptr;
+    uint32_t* err = nullptr;
+    // model and state
+    double* D = nullptr;
+    double* d_tau = nullptr;
+    int32_t* cnt = nullptr;
+    int32_t* rem = nullptr;
+    int4* out[2] = {nullptr, nullptr};
+    uint4* thr = nullptr;
+    uint4* thr_last = nullptr;
+    int32_t* staging = nullptr;
+    uint8_t* flags[2] = {nullptr, nullptr};   // active-list membership (batched engine)
+    int32_t* lists[2] = {nullptr, nullptr};   // active tets (batched engine)
+    rdk::ModelParams mp{};
+    bool has_model = false;
+    // sampled kernel timing
+    int32_t timing_stride = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    double timing_ms = 0.0;
+    int64_t timing_n = 0;
+    double tau = 0.0;
+    double t = 0.0;
+    int64_t period = 0;
+
+    rdk::DevMesh dev_mesh() const { return rdk::DevMesh{T, src, g, G, vol, mask, avv}; }
+    rdk::DevState dev_state() const { return rdk::DevState{cnt, rem, err}; }
+
+    void free_model() {
+        void* ps[] = {D, d_tau, cnt, rem, out[0], out[1], thr, thr_last, staging, mask, avv};
+        for (void* p : ps) rdapi::dev_free(p);
+        D = nullptr; d_tau = nullptr; cnt = nullptr; rem = nullptr; out[0] = out[1] = nullptr;
+        thr = nullptr; thr_last = nullptr; staging = nullptr; mask = nullptr; avv = nullptr;
+        has_model = false;
+    }
+    ~rdsplit_mesh() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        free_model();
+        void* ps[] = {src, g, G, vol, gmax, err, flags[0], flags[1], lists[0], lists[1]};
+        for (void* p : ps) rdapi::dev_free(p);
+    }
+};
+
+
+namespace rdapi {
 int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed);
+int check_err(rdsplit_mesh* h, const char* where);
 }  // namespace rdapi

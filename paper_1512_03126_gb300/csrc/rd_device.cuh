@@ -145,7 +145,7 @@ __device__ __forceinline__ double log_factorial(int64_t k) {
 // (Hoermann 1993, transformed rejection with squeeze); p > 1/2 is drawn as
 // n - Binomial(n, 1-p).
 // ------------------------------------------------------------------------
-__device__ __noinline__ int64_t binomial_inversion(int64_t n, double p, Stream& st) {
+static __device__ __noinline__ int64_t binomial_inversion(int64_t n, double p, Stream& st) {
     double q = 1.0 - p;
     double r = p / q;
     double f0 = own_exp((double)n * own_log(q));
@@ -161,7 +161,7 @@ __device__ __noinline__ int64_t binomial_inversion(int64_t n, double p, Stream& 
     return 0;
 }
 
-__device__ __noinline__ int64_t binomial_btrs(int64_t n, double p, Stream& st) {
+static __device__ __noinline__ int64_t binomial_btrs(int64_t n, double p, Stream& st) {
     double q = 1.0 - p;
     double dn = (double)n;
     double spq = sqrt(dn * p * q);

@@ -1,0 +1,681 @@
+// Batched engine: many independent simulations (mesh handles) advanced by one
+// persistent kernel, touching only tets that hold molecules.
+//
+// Realisations run in parallel are the embarrassingly parallel use of the
+// method (Sec. I of arXiv:1512.03126).  Each thread block takes one
+// simulation from a work queue (largest first) and runs its periods of
+// Algorithm 1 itself, with __syncthreads() as the period barrier, so that
+// no grid-wide synchronisation and no spin-wait is needed.  Per period the
+// block walks the simulation's list of tets that hold molecules (or have a
+// zero-order reaction on), runs the same per-tet work as the dense kernel
+// (step_tet, warp_split), and adds the molecules that stay or leave into the
+// next count buffer with integer atomic adds — exact and independent of
+// order, so the counts equal those of the dense gather.  A tet enters the
+// next list on the 0 -> 1 transition of its flag (or, with one species, of
+// its next count), so it appears once; the list counter lives in shared
+// memory.  One simulation's active region is
+// touched by one SM only, which keeps it in that SM's L1 and in L2.
+//
+// The random streams of a simulation are keyed by its own seed, period index
+// and canonical tet ids, so its counts do not depend on what runs beside it.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "rd_api_internal.h"
+#include "rd_device.cuh"
+#include "rd_internal.h"
+#include "rd_period.cuh"
+
+using namespace rdk;
+
+namespace {
+
+constexpr int kRunBlock = 512;
+
+struct SlotDesc {
+    DevMesh m;
+    const uint4* thr;        // thresholds for tau
+    const uint4* thr_last;   // thresholds for the shortened last period
+    int32_t* N[2];           // count buffers [S][T]; the slice starts in N[0]
+    uint8_t* flag[2];        // list membership, by period parity in the slice
+    int32_t* list[2];        // active tets, by period parity in the slice
+    uint64_t seed;
+    uint32_t period0;        // global period index of local period 0
+    int32_t P;               // periods to run in total
+    int32_t q0, q1;          // this slice runs local periods q0 .. q1-1
+    int32_t last_short;      // local period P-1 is shortened
+    int32_t S;
+    uint32_t zero_order;     // reactions of order 0 with k > 0
+    double tau, tau_last;
+    float tauf, tau_lastf;
+};
+
+// Flags are bytes; set one with an atomic OR on its 32-bit word.
+__device__ __forceinline__ bool set_flag(uint8_t* flags, int t) {
+    unsigned int* w = reinterpret_cast<unsigned int*>(flags + (t & ~3));
+    unsigned int bit = 1u << (8 * (t & 3));
+    unsigned int old = atomicOr(w, bit);
+    return (old & bit) == 0u;
+}
+
+__device__ __forceinline__ bool zero_order_on(const SlotDesc& d, const ModelParams& mp, int t) {
+    if (!d.zero_order) return false;
+    uint32_t on = mp.has_mask ? d.m.mask[t] : 0xffffffffu;
+    return (on & d.zero_order) != 0u;
+}
+
+// Block-wide exclusive prefix sum of small per-thread counts; *total gets
+// the block sum.  Every thread of the block must call it.
+__device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t* total, uint32_t* warp_sums) {
+    constexpr int kWarps = kRunBlock / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, dd);
+        if (lane >= dd) v += y;
+    }
+    if (lane == 31) warp_sums[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kWarps ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, dd);
+            if (lane >= dd) w += y;
+        }
+        if (lane < kWarps) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t before = (warp > 0 ? warp_sums[warp - 1] : 0u) + v - x;
+    *total = warp_sums[kWarps - 1];
+    __syncthreads();   // warp_sums is reused by the next call
+    return before;
+}
+
+// Append each thread's candidates to `list`: one atomic add per CTA on the
+// list counter *cnt, which lives in the shared memory of the cluster's first
+// CTA (a distributed-shared-memory address when the cluster has several).
+__device__ __forceinline__ void block_append(const int* cand, uint32_t ncand, int32_t* list, uint32_t capacity,
+                                             uint32_t* cnt, uint32_t* warp_sums, uint32_t* block_base,
+                                             uint32_t& bad) {
+    uint32_t total = 0;
+    uint32_t off = block_scan(ncand, &total, warp_sums);
+    if (threadIdx.x == 0) *block_base = total ? atomicAdd(cnt, total) : 0u;
+    __syncthreads();
+    const uint32_t base = *block_base;
+    for (uint32_t k = 0; k < ncand; ++k) {
+        uint32_t pos = base + off + k;
+        if (pos < capacity) list[pos] = cand[k];
+        else bad |= kErrOverflow;
+    }
+    __syncthreads();
+}
+
+// One simulation per cluster of kC CTAs (kC = 1: per CTA).  The cluster's
+// first CTA owns the work-item index and the list counters; the others read
+// and update them through distributed shared memory.  cluster.sync() (a
+// hardware barrier) separates periods.
+template <int SA, bool kReact, int kC, int kE = 1>
+__global__ void __launch_bounds__(kRunBlock, (SA <= 1 && !kReact) ? 2 : 1)
+k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__ mps, const int32_t* __restrict__ order,
+             int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed) {
+    namespace cg = cooperative_groups;
+    __shared__ int32_t item_s;
+    __shared__ uint32_t cnt_s[2];
+    __shared__ uint32_t warp_sums[kRunBlock / 32];
+    __shared__ uint32_t block_base;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
+    int32_t* item = kC > 1 ? cluster.map_shared_rank(&item_s, 0) : &item_s;
+    uint32_t* cnt = kC > 1 ? cluster.map_shared_rank(&cnt_s[0], 0) : &cnt_s[0];
+    auto csync = [&]() {
+        if (kC > 1) cluster.sync();
+        else __syncthreads();
+    };
+    unsigned long long done = 0;
+    for (;;) {
+        csync();
+        if (rank == 0 && threadIdx.x == 0) {
+            *item = atomicAdd(head, 1);
+            cnt[0] = 0;
+            cnt[1] = 0;
+        }
+        csync();
+        const int32_t k = *item;
+        // every CTA has read the item before the leader may overwrite it or
+        // any CTA leaves (a CTA's shared memory must outlive remote reads)
+        csync();
+        if (k >= n_items) break;
+        const int slot = order[k];
+        const SlotDesc d = descs[slot];
+        const ModelParams& mp = mps[slot];
+        const int T = d.m.T;
+        const int S = d.S;
+        // With one species and no zero-order reaction, a tet joins the next
+        // list when an add to its (zero) next count returns 0; otherwise a
+        // byte flag per tet marks list membership.
+        const bool by_count = (S == 1) && (d.zero_order == 0u);
+        uint32_t bad = 0;
+        // initial list: occupied tets and tets with a zero-order reaction on
+        for (int base = rank * kRunBlock; base < T; base += kC * kRunBlock) {
+            const int t = base + threadIdx.x;
+            int cand[1];
+            uint32_t nc = 0;
+            if (t < T) {
+                bool occ = kReact && zero_order_on(d, mp, t);
+                for (int s = 0; s < S && !occ; ++s) occ = d.N[0][(int64_t)s * T + t] > 0;
+                if (occ && (by_count || set_flag(d.flag[0], t))) cand[nc++] = t;
+            }
+            block_append(cand, nc, d.list[0], (uint32_t)T, &cnt[0], warp_sums, &block_base, bad);
+        }
+        for (int q = d.q0; q < d.q1; ++q) {
+            const int r = (q - d.q0) & 1;
+            csync();   // the previous period's appends are complete
+            const uint32_t n = cnt[r];
+            if (rank == 0) done += n;
+            const bool last = (q == d.P - 1) && d.last_short;
+            const double tau_k = last ? d.tau_last : d.tau;
+            const float tau_kf = last ? d.tau_lastf : d.tauf;
+            const uint4* thr = last ? d.thr_last : d.thr;
+            const uint32_t period = d.period0 + (uint32_t)q;
+            int32_t* Ncur = d.N[r];
+            int32_t* Nnext = d.N[r ^ 1];
+            const int32_t* lcur = d.list[r];
+            const bool more = q + 1 < d.q1;
+            // kE independent entries per thread and iteration, so that their
+            // memory round trips overlap
+            for (uint32_t base = (uint32_t)rank * kRunBlock * kE; base < n; base += kC * kRunBlock * kE) {
+                int cand[5 * kE];
+                uint32_t nc = 0;
+                int t[kE];
+                bool live[kE];
+                uint32_t heavy[kE];
+                int32_t N[kE][SA];
+                int4 o[kE][SA];
+#pragma unroll
+                for (int e = 0; e < kE; ++e) {
+                    const uint32_t i = base + e * kRunBlock + threadIdx.x;
+                    live[e] = i < n;
+                    t[e] = live[e] ? lcur[i] : 0;
+                    heavy[e] = 0;
+                }
+#pragma unroll
+                for (int e = 0; e < kE; ++e) {
+                    if (!live[e]) continue;
+                    if (!by_count) d.flag[r][t[e]] = 0;
+#pragma unroll
+                    for (int s = 0; s < SA; ++s) {
+                        if (s >= S) break;
+                        N[e][s] = Ncur[(int64_t)s * T + t[e]];
+                        Ncur[(int64_t)s * T + t[e]] = 0;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < kE; ++e)
+                    if (live[e])
+                        bad |= step_tet<SA, kReact>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t[e], S, N[e], o[e],
+                                                    &heavy[e], err);
+#pragma unroll
+                for (int e = 0; e < kE; ++e) warp_split<SA>(heavy[e], d.seed, period, t[e], thr, T, N[e], o[e]);
+#pragma unroll
+                for (int e = 0; e < kE; ++e) {
+                    if (!live[e]) continue;
+                    const int tt = t[e];
+                    const int4 sr = d.m.src[tt];
+                    const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
+                    bool keep = kReact && zero_order_on(d, mp, tt);
+                    bool send[4] = {false, false, false, false};
+#pragma unroll
+                    for (int s = 0; s < SA; ++s) {
+                        if (s >= S) break;
+                        int32_t* Ns = Nnext + (int64_t)s * T;
+                        if (N[e][s] > 0) {
+                            int32_t old = atomicAdd(Ns + tt, N[e][s]);
+                            if ((int64_t)old + N[e][s] > 2147483647) bad |= kErrOverflow;
+                            if (by_count && old == 0 && more) cand[nc++] = tt;
+                            keep = true;
+                        }
+                        const int ov[4] = {o[e][s].x, o[e][s].y, o[e][s].z, o[e][s].w};
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            if (ov[f] <= 0) continue;
+                            if (nbr[f] < 0) { bad |= kErrNegative; continue; }
+                            int32_t old = atomicAdd(Ns + (nbr[f] >> 2), ov[f]);
+                            if ((int64_t)old + ov[f] > 2147483647) bad |= kErrOverflow;
+                            if (by_count && old == 0 && more) cand[nc++] = nbr[f] >> 2;
+                            send[f] = true;
+                        }
+                    }
+                    if (more && !by_count) {
+                        uint8_t* fl = d.flag[r ^ 1];
+                        if (keep && set_flag(fl, tt)) cand[nc++] = tt;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f)
+                            if (send[f] && set_flag(fl, nbr[f] >> 2)) cand[nc++] = nbr[f] >> 2;
+                    }
+                }
+                block_append(cand, nc, d.list[r ^ 1], (uint32_t)T, &cnt[r ^ 1], warp_sums, &block_base, bad);
+            }
+            csync();   // every CTA has read cnt[r] and finished the period
+            // the list just walked is empty for its next use
+            if (rank == 0 && threadIdx.x == 0) cnt[r] = 0;
+        }
+        if (bad) atomicOr(err, bad);
+    }
+    if (rank == 0 && threadIdx.x == 0) atomicAdd(processed, done);
+}
+
+template <int SA, bool R, int C>
+cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParams* mps, const int32_t* order,
+                           int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed,
+                           cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * C, 1, 1);
+    cfg.blockDim = dim3(kRunBlock, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C>, descs, mps, order, n_items, head, err, processed);
+}
+
+template <int SA>
+cudaError_t launch_run_sa(bool react, int cluster, int clusters, const SlotDesc* descs, const ModelParams* mps,
+                          const int32_t* order, int32_t n_items, int32_t* head, uint32_t* err,
+                          unsigned long long* processed, cudaStream_t st) {
+    if (cluster >= 4) {
+        if (react) return launch_cluster<SA, true, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
+        return launch_cluster<SA, false, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
+    }
+    if (cluster == 2) {
+        if (react) return launch_cluster<SA, true, 2>(clusters, descs, mps, order, n_items, head, err, processed, st);
+        return launch_cluster<SA, false, 2>(clusters, descs, mps, order, n_items, head, err, processed, st);
+    }
+    if (react) k_engine_run<SA, true, 1><<<clusters, kRunBlock, 0, st>>>(descs, mps, order, n_items, head, err, processed);
+    else k_engine_run<SA, false, 1><<<clusters, kRunBlock, 0, st>>>(descs, mps, order, n_items, head, err, processed);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+struct rdsplit_engine {
+    int32_t max_slots = 0;
+    int64_t capacity = 0;
+    cudaStream_t stream = 0;
+    SlotDesc* d_desc = nullptr;
+    ModelParams* d_mp = nullptr;
+    int32_t* d_order = nullptr;
+    int32_t* d_head = nullptr;
+    uint32_t* err = nullptr;
+    unsigned long long* processed = nullptr;  // (slot, tet) entries processed so far
+    int64_t launches = 0;                     // persistent launches issued
+    int64_t steps = 0;                        // periods advanced, summed over step calls
+    int32_t timing = 0;                       // time every launch with CUDA events
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double timing_ms = 0.0;
+    int64_t timing_n = 0;
+    int sms = 1;
+    int32_t concurrency = 0;                  // simulations in flight (0 = default)
+    int32_t cluster = 4;                      // CTAs per simulation (1, 2 or 4)
+    std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
+    std::vector<SlotDesc> h_desc;
+    std::vector<int32_t> slot_q;              // local periods done
+    std::vector<double> slot_t_end;
+    std::vector<int32_t> finished;            // slots finished and not yet reported
+    int64_t active_tets = 0;
+
+    ~rdsplit_engine() {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        void* ps[] = {d_desc, d_mp, d_order, d_head, err, processed};
+        for (void* p : ps) rdapi::dev_free(p);
+    }
+};
+
+namespace {
+
+int engine_err(rdsplit_engine* e, const char* where) {
+    uint32_t v = 0;
+    cudaError_t ce = cudaMemcpyAsync(&v, e->err, sizeof v, cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "%s: %s", where, cudaGetErrorString(ce));
+    }
+    if (v == 0) return RDSPLIT_OK;
+    cudaMemsetAsync(e->err, 0, sizeof(uint32_t), e->stream);
+    if (v & kErrOverflow) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: count overflow or active-list capacity exceeded", where);
+    if (v & kErrEventCap) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: SSA event cap exceeded", where);
+    if (v & kErrNegative) return rdapi::fail(RDSPLIT_EINVAL, "%s: negative count", where);
+    return rdapi::fail(RDSPLIT_ECUDA, "%s: device error bits 0x%x", where, v);
+}
+
+// Periods to reach t_end from t with Algorithm 1 (Step 1 aligns the last one)
+// and the length of the last period.
+void plan_periods(double t, double tau, double t_end, int64_t* P, double* tau_last, bool* last_short) {
+    int64_t n = 0;
+    *tau_last = tau;
+    *last_short = false;
+    while (t < t_end) {
+        if (t + tau > t_end) {
+            *tau_last = t_end - t;
+            *last_short = true;
+            t = t_end;
+        } else {
+            t = t + tau;
+        }
+        ++n;
+    }
+    *P = n;
+}
+
+void finish_slot(rdsplit_engine* e, int slot) {
+    rdsplit_mesh* h = e->slot_mesh[slot];
+    const SlotDesc& d = e->h_desc[slot];
+    h->t = e->slot_t_end[slot];
+    h->period = (int64_t)d.period0 + d.P;
+    e->active_tets -= h->T;
+    e->slot_mesh[slot] = nullptr;
+    e->finished.push_back(slot);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_engine_t* out) {
+    if (!out) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_create: out is NULL");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > (1 << 20)) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_create: bad max_slots");
+    if (max_active_tets < 1) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_create: max_active_tets must be >= 1");
+    rdsplit_engine* e = new rdsplit_engine();
+    e->max_slots = max_slots;
+    e->capacity = max_active_tets;
+    e->d_desc = (SlotDesc*)rdapi::dev_alloc(sizeof(SlotDesc) * max_slots);
+    e->d_mp = (ModelParams*)rdapi::dev_alloc(sizeof(ModelParams) * max_slots);
+    e->d_order = (int32_t*)rdapi::dev_alloc(sizeof(int32_t) * max_slots);
+    e->d_head = (int32_t*)rdapi::dev_alloc(sizeof(int32_t));
+    e->err = (uint32_t*)rdapi::dev_alloc(sizeof(uint32_t));
+    e->processed = (unsigned long long*)rdapi::dev_alloc(sizeof(unsigned long long));
+    if (!e->d_desc || !e->d_mp || !e->d_order || !e->d_head || !e->err || !e->processed) {
+        delete e;
+        return rdapi::fail(RDSPLIT_ENOMEM, "rdsplit_engine_create: device allocation failed");
+    }
+    e->slot_mesh.assign(max_slots, nullptr);
+    e->h_desc.assign(max_slots, SlotDesc{});
+    e->slot_q.assign(max_slots, 0);
+    e->slot_t_end.assign(max_slots, 0.0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaMemsetAsync(e->processed, 0, sizeof(unsigned long long), e->stream) != cudaSuccess ||
+        cudaMemsetAsync(e->err, 0, sizeof(uint32_t), e->stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete e;
+        return rdapi::fail(RDSPLIT_ECUDA, "rdsplit_engine_create: memset failed");
+    }
+    *out = e;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_set_stream(rdsplit_engine_t e, void* stream) {
+    if (!e) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_stream: NULL engine");
+    e->stream = (cudaStream_t)stream;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_add(rdsplit_engine_t e, rdsplit_mesh_t h, double t_end, uint64_t seed, int32_t* slot_out) {
+    const char* where = "rdsplit_engine_add";
+    if (!e || !h) return rdapi::fail(RDSPLIT_EINVAL, "%s: NULL argument", where);
+    if (!h->has_model) return rdapi::fail(RDSPLIT_ESTATE, "%s: the mesh has no model", where);
+    if (std::isnan(t_end)) return rdapi::fail(RDSPLIT_EINVAL, "%s: t_end is NaN", where);
+    for (int s = 0; s < e->max_slots; ++s)
+        if (e->slot_mesh[s] == h) return rdapi::fail(RDSPLIT_EINVAL, "%s: mesh already in the engine", where);
+    int slot = -1;
+    for (int s = 0; s < e->max_slots; ++s)
+        if (!e->slot_mesh[s]) { slot = s; break; }
+    if (slot < 0) return rdapi::fail(RDSPLIT_ENOMEM, "%s: no free slot", where);
+    if (e->active_tets + h->T > e->capacity)
+        return rdapi::fail(RDSPLIT_ENOMEM, "%s: active-tet capacity %lld exceeded", where, (long long)e->capacity);
+    int64_t P = 0;
+    double tau_last = h->tau;
+    bool last_short = false;
+    plan_periods(h->t, h->tau, t_end, &P, &tau_last, &last_short);
+    if (h->period + P > (int64_t)0xffffffffll) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: period index exceeds 2^32-1", where);
+    if (P > 0x7fffffffll) return rdapi::fail(RDSPLIT_EINVAL, "%s: too many periods", where);
+    const size_t T = (size_t)h->T;
+    if (!h->flags[0]) {
+        h->flags[0] = (uint8_t*)rdapi::dev_alloc(T + 4);
+        h->flags[1] = (uint8_t*)rdapi::dev_alloc(T + 4);
+        h->lists[0] = (int32_t*)rdapi::dev_alloc(4 * T);
+        h->lists[1] = (int32_t*)rdapi::dev_alloc(4 * T);
+        if (!h->flags[0] || !h->flags[1] || !h->lists[0] || !h->lists[1])
+            return rdapi::fail(RDSPLIT_ENOMEM, "%s: list allocation failed", where);
+    }
+    cudaStream_t st = e->stream;
+    cudaError_t ce = cudaMemsetAsync(h->flags[0], 0, T + 4, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->flags[1], 0, T + 4, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->rem, 0, sizeof(int32_t) * T * h->S, st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "%s: memset failed: %s", where, cudaGetErrorString(ce));
+    }
+    if (last_short) launch_thresholds(h->T, h->mp, h->g, h->G, tau_last, h->thr_last, st);
+    SlotDesc d{};
+    d.m = h->dev_mesh();
+    d.thr = h->thr;
+    d.thr_last = last_short ? h->thr_last : h->thr;
+    d.N[0] = h->cnt;
+    d.N[1] = h->rem;
+    d.flag[0] = h->flags[0];
+    d.flag[1] = h->flags[1];
+    d.list[0] = h->lists[0];
+    d.list[1] = h->lists[1];
+    d.seed = seed;
+    d.period0 = (uint32_t)h->period;
+    d.P = (int32_t)P;
+    d.q0 = d.q1 = 0;
+    d.last_short = last_short ? 1 : 0;
+    d.S = h->S;
+    d.zero_order = 0;
+    for (int r = 0; r < h->R; ++r)
+        if (h->mp.order[r] == 0 && h->mp.k[r] > 0.0) d.zero_order |= 1u << r;
+    d.tau = h->tau;
+    d.tau_last = tau_last;
+    d.tauf = (float)h->tau;
+    d.tau_lastf = (float)tau_last;
+    ce = cudaMemcpyAsync(e->d_mp + slot, &h->mp, sizeof(ModelParams), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "%s: model upload failed: %s", where, cudaGetErrorString(ce));
+    }
+    e->h_desc[slot] = d;
+    e->slot_mesh[slot] = h;
+    e->slot_q[slot] = 0;
+    e->slot_t_end[slot] = t_end;
+    e->active_tets += h->T;
+    if (P == 0) finish_slot(e, slot);
+    if (slot_out) *slot_out = slot;
+    return RDSPLIT_OK;
+}
+
+// Advance every active simulation by up to n_steps periods in one persistent
+// launch.  Finished handles receive their counts, time and period index;
+// their slot ids are queued for rdsplit_engine_poll.
+int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
+    const char* where = "rdsplit_engine_step";
+    if (!e) return rdapi::fail(RDSPLIT_EINVAL, "%s: NULL engine", where);
+    if (n_steps <= 0) return RDSPLIT_OK;
+    std::vector<int32_t> items;
+    std::vector<double> work;
+    int maxS = 1;
+    bool react = false;
+    int64_t max_adv = 0;
+    for (int s = 0; s < e->max_slots; ++s) {
+        rdsplit_mesh* h = e->slot_mesh[s];
+        if (!h) continue;
+        SlotDesc& d = e->h_desc[s];
+        d.q0 = e->slot_q[s];
+        d.q1 = (int32_t)std::min<int64_t>((int64_t)d.P, (int64_t)d.q0 + n_steps);
+        if (d.q1 <= d.q0) continue;
+        items.push_back(s);
+        work.push_back((double)(d.q1 - d.q0) * (double)h->T);
+        maxS = std::max(maxS, d.S);
+        react = react || h->R > 0;
+        max_adv = std::max<int64_t>(max_adv, d.q1 - d.q0);
+    }
+    if (items.empty()) return engine_err(e, where);
+    // largest first
+    std::vector<size_t> idx(items.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+    std::vector<int32_t> order(items.size());
+    for (size_t k = 0; k < idx.size(); ++k) order[k] = items[idx[k]];
+    cudaStream_t st = e->stream;
+    cudaError_t ce = cudaMemcpyAsync(e->d_desc, e->h_desc.data(), sizeof(SlotDesc) * e->max_slots,
+                                     cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(e->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->d_head, 0, sizeof(int32_t), st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "%s: upload failed: %s", where, cudaGetErrorString(ce));
+    }
+    const int n_items = (int)order.size();
+    const int csize = e->cluster;
+    // default: about one simulation per 4.75 SMs (32 on 152), which keeps the
+    // simulations' scattered working sets within L2 (measured optimum)
+    const int in_flight = e->concurrency > 0 ? e->concurrency : std::max(1, (e->sms * 4) / 19);
+    const int clusters = std::min(n_items, in_flight);
+    if (e->timing && !e->ev[0]) {
+        cudaEventCreate(&e->ev[0]);
+        cudaEventCreate(&e->ev[1]);
+    }
+    if (e->timing) cudaEventRecord(e->ev[0], st);
+    int32_t* ord = e->d_order;
+    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    if (e->timing) cudaEventRecord(e->ev[1], st);
+    note_launch();
+    e->launches += 1;
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "%s: launch failed: %s", where, cudaGetErrorString(ce));
+    }
+    int rc = engine_err(e, where);
+    if (e->timing) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e->ev[0], e->ev[1]) == cudaSuccess) {
+            e->timing_ms += ms;
+            e->timing_n += 1;
+        }
+        cudaGetLastError();
+    }
+    e->steps += max_adv;
+    // the slice leaves each simulation's counts in N[(q1 - q0) & 1]
+    for (int32_t s : items) {
+        SlotDesc& d = e->h_desc[s];
+        rdsplit_mesh* h = e->slot_mesh[s];
+        if ((d.q1 - d.q0) & 1) {
+            std::swap(d.N[0], d.N[1]);
+            std::swap(h->cnt, h->rem);
+        }
+        e->slot_q[s] = d.q1;
+        if (d.q1 == d.P) finish_slot(e, s);
+    }
+    return rc;
+}
+
+int rdsplit_engine_poll(rdsplit_engine_t e, int32_t* slots, int32_t max, int32_t* n_out) {
+    if (!e || !n_out) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_poll: NULL argument");
+    int32_t n = 0;
+    while (n < max && !e->finished.empty()) {
+        slots[n++] = e->finished.front();
+        e->finished.erase(e->finished.begin());
+    }
+    *n_out = n;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_active(rdsplit_engine_t e, int32_t* n_slots, int64_t* n_tets) {
+    if (!e) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_active: NULL engine");
+    int32_t n = 0;
+    for (int s = 0; s < e->max_slots; ++s) n += e->slot_mesh[s] ? 1 : 0;
+    if (n_slots) *n_slots = n;
+    if (n_tets) *n_tets = e->active_tets;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_t cluster) {
+    if (!e || in_flight < 0 || !(cluster == 1 || cluster == 2 || cluster == 4))
+        return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_concurrency: bad argument");
+    e->concurrency = in_flight;
+    e->cluster = cluster;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_set_timing(rdsplit_engine_t e, int32_t on) {
+    if (!e || on < 0) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_timing: bad argument");
+    e->timing = on;
+    e->timing_ms = 0.0;
+    e->timing_n = 0;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_stats(rdsplit_engine_t e, int64_t* steps, int64_t* processed, double* timing_ms,
+                         int64_t* timing_n) {
+    if (!e) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_stats: NULL engine");
+    unsigned long long p = 0;
+    cudaError_t ce = cudaMemcpyAsync(&p, e->processed, sizeof p, cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "rdsplit_engine_stats: %s", cudaGetErrorString(ce));
+    }
+    if (steps) *steps = e->steps;
+    if (processed) *processed = (int64_t)p;
+    if (timing_ms) *timing_ms = e->timing_ms;
+    if (timing_n) *timing_n = e->timing_n;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_destroy(rdsplit_engine_t e) {
+    if (!e) return RDSPLIT_OK;
+    cudaStreamSynchronize(e->stream);
+    delete e;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_ensemble_run(int32_t n, const rdsplit_mesh_t* meshes, const double* t_end, const uint64_t* seeds) {
+    const char* where = "rdsplit_ensemble_run";
+    if (n < 1 || !meshes || !t_end || !seeds) return rdapi::fail(RDSPLIT_EINVAL, "%s: bad arguments", where);
+    int64_t tets = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!meshes[i]) return rdapi::fail(RDSPLIT_EINVAL, "%s: NULL mesh %d", where, i);
+        tets += meshes[i]->T;
+    }
+    rdsplit_engine_t e = nullptr;
+    int rc = rdsplit_engine_create(n, tets, &e);
+    if (rc) return rc;
+    e->stream = meshes[0]->stream;
+    for (int i = 0; i < n && rc == RDSPLIT_OK; ++i) rc = rdsplit_engine_add(e, meshes[i], t_end[i], seeds[i], nullptr);
+    if (rc == RDSPLIT_OK) rc = rdsplit_engine_step(e, INT64_MAX / 4);
+    rdsplit_engine_destroy(e);
+    return rc;
+}
+
+}  // extern "C"

@@ -31,7 +31,15 @@ struct ModelParams {
     int8_t lhs[kMaxR][kMaxS];
     int8_t delta[kMaxR][kMaxS];   // rhs - lhs
     int8_t order[kMaxR];
+    // For the single-precision "no event this period" pre-test: reactant
+    // species (-1 = none; rs1 == rs2 for 2A), k as float, bits of k > 0.
+    int8_t rs1[kMaxR], rs2[kMaxR];
+    float kf[kMaxR];
+    uint32_t kpos;
 };
+
+// Fill the pre-test fields of a ModelParams whose lhs/k/order are set.
+void finish_model_params(ModelParams& mp);
 
 // Device arrays of one mesh + state.  Counts are species-major ([S][T]);
 // out-slots are [S][T][4]; src[t][f] = 4*adj[t][f] + (slot of t in that
@@ -43,6 +51,7 @@ struct DevMesh {
     const double* G;        // [T]   sum of g
     const double* vol;      // [T]
     const uint32_t* mask;   // [T]   reaction-on bits, or null
+    const float2* avv;      // [T]   (N_A V_L, 1/(N_A V_L)) in single precision, or null
 };
 
 struct DevState {
@@ -59,6 +68,7 @@ void launch_tau(const double* D, int32_t S, const unsigned long long* gmax_bits,
                 double* tau_out, cudaStream_t st);
 void launch_thresholds(int32_t T, const ModelParams& mp, const double* g, const double* G, double tau_k,
                        uint4* thr, cudaStream_t st);
+void launch_avv(int32_t T, const double* vol, float2* avv, cudaStream_t st);
 void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, cudaStream_t st);
 void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* st_major, uint32_t* err,
                       cudaStream_t st);
@@ -69,6 +79,7 @@ void launch_counts_out(int32_t T, int32_t S, const int32_t* st_major, int32_t* t
 struct PeriodArgs {
     uint32_t period;        // global period index (random-stream key)
     double tau_k;           // length of this period
+    float tau_kf;           // tau_k rounded to single precision
     uint64_t seed;
     int32_t first;          // 1: counts come from cnt (no pending transfer)
     const uint4* thr;       // [S][T] cumulative 32-bit face thresholds for tau_k

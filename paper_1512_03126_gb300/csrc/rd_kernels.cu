@@ -169,50 +169,95 @@ void launch_counts_out(int32_t T, int32_t S, const int32_t* sm, int32_t* ts, cud
 }
 
 // ---------------------------------------------------------------- period ---
-template <bool kReact>
-__global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, DevState s, PeriodArgs a) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.T) return;
-    const int T = m.T;
-    int4 sr = m.src[t];
-    int64_t N[kMaxS];
-    uint32_t bad = 0;
-    for (int sp = 0; sp < mp.S; ++sp) {
-        int64_t n;
-        if (a.first) {
-            n = s.cnt[(int64_t)sp * T + t];
-        } else {
-            n = s.rem[(int64_t)sp * T + t] +
-                incoming(reinterpret_cast<const int32_t*>(a.out_prev + (int64_t)sp * T), sr);
+void finish_model_params(ModelParams& mp) {
+    mp.kpos = 0;
+    for (int r = 0; r < mp.R; ++r) {
+        mp.rs1[r] = mp.rs2[r] = -1;
+        for (int s = 0; s < mp.S; ++s) {
+            if (mp.lhs[r][s] == 2) { mp.rs1[r] = mp.rs2[r] = (int8_t)s; }
+            else if (mp.lhs[r][s] == 1) {
+                if (mp.rs1[r] < 0) mp.rs1[r] = (int8_t)s;
+                else mp.rs2[r] = (int8_t)s;
+            }
         }
-        if (n > 2147483647) { bad |= kErrOverflow; n = 2147483647; }
-        if (n < 0) { bad |= kErrNegative; n = 0; }
-        N[sp] = n;
+        mp.kf[r] = (float)mp.k[r];
+        if (mp.k[r] > 0.0) mp.kpos |= 1u << r;
     }
-    double occ[kMaxS], tl[kMaxS];
-    uint32_t touched = 0;
-    if (kReact) {
-        for (int sp = 0; sp < mp.S; ++sp) { occ[sp] = 0.0; tl[sp] = 0.0; }
-        react_tet(m, mp, t, a.period, a.tau_k, a.seed, N, occ, tl, touched, s.err);
+}
+
+__global__ void k_avv(int32_t T, const double* __restrict__ vol, float2* __restrict__ avv) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    double a = kAvogadro * (vol[t] * 1000.0);
+    avv[t] = make_float2((float)a, (float)(1.0 / a));
+}
+
+void launch_avv(int32_t T, const double* vol, float2* avv, cudaStream_t st) {
+    k_avv<<<grid_for(T), kBlock, 0, st>>>(T, vol, avv);
+    ++g_launches;
+}
+
+// One period for one tet: apply the previous period's transfers, run the
+// reaction phase, draw the diffusion out-counts.  S_ > 0 fixes the species
+// count at compile time so that counts live in registers; S_ = 0 reads it
+// from the model (up to kMaxS).
+template <int S_, bool kReact>
+__global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, DevState s, PeriodArgs a) {
+    constexpr int SA = S_ > 0 ? S_ : kMaxS;
+    const int S = S_ > 0 ? S_ : mp.S;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < m.T;          // every lane stays for the warp draw
+    const int T = m.T;
+    int32_t N[SA];
+    int4 o[SA];
+    uint32_t bad = 0, heavy = 0;
+    if (valid) {
+        int4 sr = m.src[t];
+#pragma unroll
+        for (int sp = 0; sp < SA; ++sp) {
+            if (sp >= S) break;
+            int64_t n;
+            if (a.first) {
+                n = s.cnt[(int64_t)sp * T + t];
+            } else {
+                n = (int64_t)s.rem[(int64_t)sp * T + t] +
+                    incoming(reinterpret_cast<const int32_t*>(a.out_prev + (int64_t)sp * T), sr);
+            }
+            if (n > 2147483647) { bad |= kErrOverflow; n = 2147483647; }
+            if (n < 0) { bad |= kErrNegative; n = 0; }
+            N[sp] = (int32_t)n;
+        }
+        bad |= step_tet<SA, kReact>(m, mp, a.period, a.tau_k, a.tau_kf, a.seed, a.thr, t, S, N, o, &heavy, s.err);
     }
-    for (int sp = 0; sp < mp.S; ++sp) {
-        int64_t Nt = N[sp];
-        if (Nt < 0) { bad |= kErrNegative; Nt = 0; }
-        uint4 C = a.thr[(int64_t)sp * T + t];
-        bool tch = kReact && ((touched >> sp) & 1u);
-        int4 o = diffuse(m, t, sp, mp.D[sp], a.period, a.tau_k, a.seed, Nt, tch, kReact ? occ[sp] : 0.0, C);
-        a.out_cur[(int64_t)sp * T + t] = o;
-        int64_t r = Nt - ((int64_t)o.x + o.y + o.z + o.w);
-        if (r > 2147483647) { bad |= kErrOverflow; r = 2147483647; }
-        s.rem[(int64_t)sp * T + t] = (int32_t)r;
+    warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
+    if (valid) {
+#pragma unroll
+        for (int sp = 0; sp < SA; ++sp) {
+            if (sp >= S) break;
+            a.out_cur[(int64_t)sp * T + t] = o[sp];
+            s.rem[(int64_t)sp * T + t] = N[sp];
+        }
+        if (bad) atomicOr(s.err, bad);
     }
-    if (bad) atomicOr(s.err, bad);
+}
+
+template <int S_>
+void launch_period_s(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+                     cudaStream_t st) {
+    if (mp.any_reaction) k_period<S_, true><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
+    else k_period<S_, false><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
 }
 
 void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
                    cudaStream_t st) {
-    if (mp.any_reaction) k_period<true><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
-    else k_period<false><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
+    switch (mp.S) {
+        case 1: launch_period_s<1>(m, mp, s, a, st); break;
+        case 2: launch_period_s<2>(m, mp, s, a, st); break;
+        case 3: launch_period_s<3>(m, mp, s, a, st); break;
+        case 4: launch_period_s<4>(m, mp, s, a, st); break;
+        case 8: launch_period_s<8>(m, mp, s, a, st); break;
+        default: launch_period_s<0>(m, mp, s, a, st); break;
+    }
     ++g_launches;
 }
 

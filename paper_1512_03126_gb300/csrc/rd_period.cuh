@@ -7,6 +7,13 @@
 namespace rdk {
 
 constexpr int kEventCap = 1 << 22;   // SSA events per tet and period
+// Below this N* the diffusion draw is one uniform per molecule (the paper's
+// per-molecule form, Sec. II.B); at or above it, Binomial + conditional
+// binomials in double precision.
+constexpr int64_t kMoleculeCut = 4096;
+// From this N* up to kMoleculeCut, a warp draws the molecules of one tet
+// together (untouched species only).
+constexpr int32_t kWarpSplitMin = 10;
 constexpr double kAvogadro = 6.02214076e23;
 
 // Transfer probability over a period of length tau_k (Eq. 1 and the text
@@ -31,7 +38,7 @@ __device__ __forceinline__ int64_t incoming(const int32_t* __restrict__ op, int4
 // direct method over [0, tau_k); the first event at or past tau_k is
 // discarded.  Before a species' count changes, its occupancy integral
 // advances by N * (t_event - t_last).
-__device__ __forceinline__ void react_tet(const DevMesh& m, const ModelParams& mp, int t, uint32_t period,
+static __device__ __noinline__ void react_tet(const DevMesh& m, const ModelParams& mp, int t, uint32_t period,
                                           double tau_k, uint64_t seed, int64_t* N, double* occ, double* tl,
                                           uint32_t& touched, uint32_t* err) {
     double avv = kAvogadro * (m.vol[t] * 1000.0);
@@ -94,9 +101,9 @@ __device__ __forceinline__ void react_tet(const DevMesh& m, const ModelParams& m
 // Diffusion of one species out of one tet (Algorithm 1, Step 3; Eq. 2-3;
 // Sec. II.B): N* from the occupancy (stochastic rounding of N-bar when the
 // count changed during the period, else N), n = min(Binomial(N*, zeta), N),
-// split over the faces by conditional binomials; below N* = 10 the same law
-// one molecule at a time against the cumulative thresholds.
-__device__ __forceinline__ int4 diffuse(const DevMesh& m, int t, int s, double Dsp, uint32_t period, double tau_k,
+// split over the faces by conditional binomials; below N* = kMoleculeCut the
+// same law one molecule at a time against the cumulative thresholds.
+static __device__ __noinline__ int4 diffuse(const DevMesh& m, int t, int s, double Dsp, uint32_t period, double tau_k,
                                         uint64_t seed, int64_t Nt, bool touched, double occ, uint4 C) {
     int4 o = make_int4(0, 0, 0, 0);
     double Gt = m.G[t];
@@ -112,7 +119,7 @@ __device__ __forceinline__ int4 diffuse(const DevMesh& m, int t, int s, double D
     }
     if (Nstar <= 0) return o;
     rdd::Stream ds(seed, (uint32_t)t, period, rdd::kPurposeDiffusion, (uint32_t)s);
-    if (Nstar < 10) {
+    if (Nstar < kMoleculeCut) {
         int64_t moved = 0;
         for (int64_t i = 0; i < Nstar; ++i) {
             if (moved == Nt) break;
@@ -146,6 +153,211 @@ __device__ __forceinline__ int4 diffuse(const DevMesh& m, int t, int s, double D
     }
     o = make_int4((int)nf[0], (int)nf[1], (int)nf[2], (int)nf[3]);
     return o;
+}
+
+// N[i] for a runtime index without dynamic register indexing (which would
+// move the array to local memory).
+template <int SA>
+__device__ __forceinline__ int32_t pick(const int32_t* N, int i) {
+    int32_t v = 0;
+#pragma unroll
+    for (int k = 0; k < SA; ++k)
+        if (k == i) v = N[k];
+    return v;
+}
+
+// Number of distinct reactant combinations of reaction r as a float (0 when a
+// reactant is missing).
+template <int SA>
+__device__ __forceinline__ float combos_f(const ModelParams& mp, int r, const int32_t* N) {
+    int a = mp.rs1[r], b = mp.rs2[r];
+    if (a < 0) return 1.0f;
+    int32_t na = pick<SA>(N, a);
+    if (b < 0) return (float)na;
+    if (a == b) return na >= 2 ? 0.5f * (float)na * (float)(na - 1) : 0.0f;
+    return (float)na * (float)pick<SA>(N, b);
+}
+
+// True only if the exact SSA of this tet would draw no event in this period:
+// with u1 the stream's first uniform, the first event time is
+// -log(u1)/a0 >= (1-u1)/a0, so (1-u1) >= a0 tau_k (1 + margin) rules an event
+// out.  a0 and the products are evaluated in single precision; their relative
+// error (< 3e-6 for 32 reactions) and that of the double-precision path
+// (< 1e-13) sit far inside the 1e-4 margin, and 1-u1 is bounded from below by
+// truncating its 53-bit integer to 24 bits, so the decision never differs
+// from the double-precision one.  Any doubtful case returns false and the
+// exact path runs.
+template <int SA>
+__device__ __forceinline__ bool surely_no_event(const ModelParams& mp, const int32_t* N, uint32_t on, float2 av,
+                                                uint32_t period, float tau_kf, uint64_t seed, int t) {
+    float a0 = 0.0f;
+    const int R = mp.R;
+    for (int r = 0; r < R; ++r) {
+        if (!((on >> r) & 1u)) continue;
+        float h = combos_f<SA>(mp, r, N);
+        if (h == 0.0f) continue;
+        int o = mp.order[r];
+        float c = o == 0 ? mp.kf[r] * av.x : (o == 1 ? mp.kf[r] : mp.kf[r] * av.y);
+        a0 += c * h;
+    }
+    rdd::Stream st(seed, (uint32_t)t, period, rdd::kPurposeReaction, 0);
+    uint64_t x = st.bits53();
+    uint64_t y = 9007199254740991ull - x;     // (1 - u1) * 2^53
+    uint32_t yhi = (uint32_t)(y >> 29);       // top 24 bits: yhi * 2^-24 <= 1 - u1
+    if (yhi == 0) return false;
+    float lo = (float)yhi * 5.9604644775390625e-08f;
+    float need = a0 * tau_kf * 1.0001f;
+    return need < 3.0e38f && lo >= need;
+}
+
+// One draw per molecule against the cumulative face thresholds (N* < 10 and
+// the count untouched by reactions, so N* = N).
+__device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, int t, int sp, int32_t n, uint4 C) {
+    int4 o = make_int4(0, 0, 0, 0);
+    if (C.w == 0u) return o;                 // nothing can leave (zeta * 2^32 < 1)
+    rdd::Stream ds(seed, (uint32_t)t, period, rdd::kPurposeDiffusion, (uint32_t)sp);
+    for (int i = 0; i < n; ++i) {
+        uint32_t u = ds.u32();
+        if (rdd::below(u, C.x)) o.x += 1;
+        else if (rdd::below(u, C.y)) o.y += 1;
+        else if (rdd::below(u, C.z)) o.z += 1;
+        else if (rdd::below(u, C.w)) o.w += 1;
+    }
+    return o;
+}
+
+
+// Steps 2 and 3 of one period for one tet, given its counts N after the
+// previous period's transfers: the reaction phase (skipped when no reaction
+// can fire or the single-precision test proves that none fires), then the
+// diffusion draws of every species.  On return N holds the molecules that
+// stay and o[s] the molecules leaving through each face, except for the
+// species whose bit is set in *heavy: those (untouched, 10 <= N < 4096) are
+// left for warp_split, which the whole warp must call next.  Returns error
+// bits.
+template <int SA, bool kReact>
+__device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams& mp, uint32_t period, double tau_k,
+                                             float tau_kf, uint64_t seed, const uint4* __restrict__ thr, int t,
+                                             int S, int32_t* N, int4* o, uint32_t* heavy, uint32_t* err) {
+    const int64_t T = m.T;
+    uint32_t bad = 0;
+    uint32_t touched = 0;
+    double occ[SA];
+    if (kReact) {
+        uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
+        bool possible = false;
+        for (int r = 0; r < mp.R && !possible; ++r) {
+            if (!((on >> r) & 1u)) continue;
+            int ra = mp.rs1[r], rb = mp.rs2[r];
+            int32_t na = ra < 0 ? 1 : pick<SA>(N, ra);
+            int32_t nb = rb < 0 ? 1 : pick<SA>(N, rb);
+            possible = ra < 0 || (rb < 0 ? na > 0 : (ra == rb ? na > 1 : (na > 0 && nb > 0)));
+        }
+        if (possible && !surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, t)) {
+            int64_t N64[SA];
+            double tl[SA];
+#pragma unroll
+            for (int sp = 0; sp < SA; ++sp) {
+                if (sp >= S) break;
+                N64[sp] = N[sp];
+                occ[sp] = 0.0;
+                tl[sp] = 0.0;
+            }
+            react_tet(m, mp, t, period, tau_k, seed, N64, occ, tl, touched, err);
+#pragma unroll
+            for (int sp = 0; sp < SA; ++sp) {
+                if (sp >= S) break;
+                int64_t v = N64[sp];
+                if (v < 0) { bad |= kErrNegative; v = 0; }
+                if (v > 2147483647) { bad |= kErrOverflow; v = 2147483647; }
+                N[sp] = (int32_t)v;
+            }
+        }
+    }
+#pragma unroll
+    for (int sp = 0; sp < SA; ++sp) {
+        if (sp >= S) break;
+        int32_t Nt = N[sp];
+        int4 x = make_int4(0, 0, 0, 0);
+        bool tch = kReact && ((touched >> sp) & 1u);
+        if (Nt > 0) {
+            if (!tch && Nt < kWarpSplitMin) {
+                x = split_molecules(seed, period, t, sp, Nt, thr[sp * T + t]);
+            } else if (!tch && Nt < kMoleculeCut) {
+                *heavy |= 1u << sp;        // drawn by the whole warp (warp_split)
+                o[sp] = x;
+                continue;
+            } else {
+                x = diffuse(m, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0, thr[sp * T + t]);
+            }
+        }
+        o[sp] = x;
+        N[sp] = Nt - (x.x + x.y + x.z + x.w);
+    }
+    return bad;
+}
+
+
+// The per-molecule draw of one (tet, species) spread over a warp: lane l
+// computes Philox blocks l, l+32, ... of the tet's diffusion stream (block b
+// holds the uniforms of molecules 4b..4b+3, exactly the words the sequential
+// draw would use) and the face counts are summed over the warp.  Every lane
+// of the warp must call this; lanes with heavy == 0 only help.
+template <int SA>
+__device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32_t period, int t,
+                                           const uint4* __restrict__ thr, int64_t T, int32_t* N, int4* o) {
+    const unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned m = __ballot_sync(kAll, heavy != 0u);
+        if (m == 0u) break;
+        const int src = __ffs(m) - 1;
+        const int my_sp = heavy ? __ffs(heavy) - 1 : 0;
+        uint4 myC = make_uint4(0, 0, 0, 0);
+        if (lane == src) myC = thr[my_sp * T + t];
+        const int sp = __shfl_sync(kAll, my_sp, src);
+        const int32_t n = __shfl_sync(kAll, pick<SA>(N, my_sp), src);
+        const int tt = __shfl_sync(kAll, t, src);
+        const uint32_t pr = __shfl_sync(kAll, period, src);
+        const uint32_t k0 = __shfl_sync(kAll, (uint32_t)seed, src);
+        const uint32_t k1 = __shfl_sync(kAll, (uint32_t)(seed >> 32), src);
+        uint4 C;
+        C.x = __shfl_sync(kAll, myC.x, src);
+        C.y = __shfl_sync(kAll, myC.y, src);
+        C.z = __shfl_sync(kAll, myC.z, src);
+        C.w = __shfl_sync(kAll, myC.w, src);
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        if (C.w != 0u) {
+            const uint32_t tag = (rdd::kPurposeDiffusion << 16) | (uint32_t)sp;
+            const int nblocks = (n + 3) >> 2;
+            for (int b = lane; b < nblocks; b += 32) {
+                uint4 w = rdd::philox_block((uint32_t)b, (uint32_t)tt, pr, tag, k0, k1);
+                const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (4 * b + q >= n) break;
+                    if (rdd::below(u[q], C.x)) ++c0;
+                    else if (rdd::below(u[q], C.y)) ++c1;
+                    else if (rdd::below(u[q], C.z)) ++c2;
+                    else if (rdd::below(u[q], C.w)) ++c3;
+                }
+            }
+        }
+        c0 = __reduce_add_sync(kAll, c0);
+        c1 = __reduce_add_sync(kAll, c1);
+        c2 = __reduce_add_sync(kAll, c2);
+        c3 = __reduce_add_sync(kAll, c3);
+        if (lane == src) {
+#pragma unroll
+            for (int k = 0; k < SA; ++k) {
+                if (k == sp) {
+                    o[k] = make_int4(c0, c1, c2, c3);
+                    N[k] -= c0 + c1 + c2 + c3;
+                }
+            }
+            heavy &= ~(1u << sp);
+        }
+    }
 }
 
 }  // namespace rdk

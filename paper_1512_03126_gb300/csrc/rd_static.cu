@@ -56,7 +56,7 @@ int scratch_base(unsigned char** out) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t err, gmax, tau, src, g, G, mask, cnt, rem, out0, out1, thr, total;
+    size_t err, gmax, tau, src, g, G, avv, mask, cnt, rem, out0, out1, thr, total;
 };
 
 Layout layout_for(size_t T, size_t S, bool masked) {
@@ -68,6 +68,7 @@ Layout layout_for(size_t T, size_t S, bool masked) {
     L.src = o;  o = align256(o + 16 * T);
     L.g = o;    o = align256(o + 32 * T);
     L.G = o;    o = align256(o + 8 * T);
+    L.avv = o;  o = align256(o + 8 * T);
     L.mask = o; o = align256(o + (masked ? 4 * T : 0));
     L.cnt = o;  o = align256(o + 4 * T * S);
     L.rem = o;  o = align256(o + 4 * T * S);
@@ -121,6 +122,7 @@ int model_params(int32_t S, const double* D, int32_t R, const int32_t* lhs, cons
     }
     mp->any_reaction = R > 0 ? 1 : 0;
     mp->has_mask = mask ? 1 : 0;
+    finish_model_params(*mp);
     return RDSPLIT_OK;
 }
 
@@ -179,6 +181,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     int4* src = (int4*)(base + L.src);
     double* g = (double*)(base + L.g);
     double* G = (double*)(base + L.G);
+    float2* avv = (float2*)(base + L.avv);
     uint32_t* mask32 = d_rxn_tet_mask ? (uint32_t*)(base + L.mask) : nullptr;
     int32_t* cnt = (int32_t*)(base + L.cnt);
     int32_t* rem = (int32_t*)(base + L.rem);
@@ -195,6 +198,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     k_static_tau<<<1, 32, 0, st>>>(mp, gmax, tau_scale, d_tau);
     note_launch();
     if (mask32) launch_pack_mask(n_tets, n_reactions, d_rxn_tet_mask, mask32, st);
+    launch_avv(n_tets, d_vol, avv, st);
     double tau = 0.0;
     ce = cudaMemcpyAsync(&tau, d_tau, sizeof tau, cudaMemcpyDeviceToHost, st);
     if (ce != cudaSuccess) {
@@ -203,7 +207,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     }
     if ((rc = read_err(base, L, st, where))) return rc;
 
-    DevMesh m{n_tets, src, g, G, d_vol, mask32};
+    DevMesh m{n_tets, src, g, G, d_vol, mask32, avv};
     DevState s{cnt, rem, err};
     launch_counts_in(n_tets, n_species, d_counts, cnt, err, st);
     if (std::isfinite(tau)) launch_thresholds(n_tets, mp, g, G, tau, thr, st);
@@ -224,7 +228,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
         }
         if (last) launch_thresholds(n_tets, mp, g, G, tau_k, thr, st);
         int4* cur = out[j & 1];
-        PeriodArgs a{(uint32_t)pk, tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
+        PeriodArgs a{(uint32_t)pk, tau_k, (float)tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
         launch_period(m, mp, s, a, st);
         prev = cur;
         tn = last ? t_end : tn + tau;

@@ -9,7 +9,8 @@ placement, instance sizes) comes from numpy's PCG64 with explicit seeds.
 
 Meshes are Kuhn (Freudenthal) subdivisions of a box of cells: every cell is
 split into 6 tetrahedra along its main diagonal, one per permutation of the
-axes.  The paper's own meshes (a spiny dendrite, a cylinder; Sec. II.A and
+axes.  Cells are numbered along a Morton (Z-order) curve, as a
+locality-preserving mesh numbering would be.  The paper's own meshes (a spiny dendrite, a cylinder; Sec. II.A and
 Sec. III.D) are not available, so these boxes stand in for them.
 
 Conventions (also those of the C ABI):
@@ -22,6 +23,7 @@ Conventions (also those of the C ABI):
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -74,14 +76,33 @@ class Model:
         return int(self.k.shape[0])
 
 
+def _spread3(x: np.ndarray) -> np.ndarray:
+    """Spread the low 21 bits of x so that bit b lands on bit 3b."""
+    x = x.astype(np.uint64) & np.uint64(0x1FFFFF)
+    x = (x | (x << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+    x = (x | (x << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+    x = (x | (x << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+    x = (x | (x << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+    x = (x | (x << np.uint64(2))) & np.uint64(0x1249249249249249)
+    return x
+
+
+def _morton3(i, j, k) -> np.ndarray:
+    return _spread3(i) | (_spread3(j) << np.uint64(1)) | (_spread3(k) << np.uint64(2))
+
+
+@functools.lru_cache(maxsize=64)
 def _topology(nx: int, ny: int, nz: int):
-    """Vertex ids of every tet (canonical order: cell raster, x fastest, then
-    the 6 permutations) and the face adjacency."""
+    """Vertex ids of every tet (canonical order: cells along a Morton curve,
+    then the 6 permutations of each cell) and the face adjacency."""
     ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
-    # cell raster with x fastest
-    ci = ii.transpose(2, 1, 0).reshape(-1)
-    cj = jj.transpose(2, 1, 0).reshape(-1)
-    ck = kk.transpose(2, 1, 0).reshape(-1)
+    ci = ii.reshape(-1)
+    cj = jj.reshape(-1)
+    ck = kk.reshape(-1)
+    # cells along a Morton (Z-order) curve, so that a ball of cells is a
+    # compact range of tet ids
+    order = np.argsort(_morton3(ci, cj, ck), kind="stable")
+    ci, cj, ck = ci[order], cj[order], ck[order]
     ncell = ci.shape[0]
     sx, sy = 1, nx + 1
     sz = (nx + 1) * (ny + 1)
@@ -108,7 +129,10 @@ def _topology(nx: int, ny: int, nz: int):
     adj = np.full(T * 4, -1, dtype=np.int64)
     adj[a] = b // 4
     adj[b] = a // 4
-    return verts, adj.reshape(T, 4).astype(np.int32)
+    adj = adj.reshape(T, 4).astype(np.int32)
+    verts.setflags(write=False)
+    adj.setflags(write=False)
+    return verts, adj
 
 
 def kuhn_box(nx: int, ny: int, nz: int, size=(1e-6, 1e-6, 1e-6),
@@ -171,7 +195,7 @@ def kuhn_box(nx: int, ny: int, nz: int, size=(1e-6, 1e-6, 1e-6),
     dv = nbc - cen[:, None, :]
     dist = np.sqrt(np.einsum("ijk,ijk->ij", dv, dv))
     dist[adj < 0] = 0.0
-    return Mesh(adj=np.ascontiguousarray(adj), vol=vol, area=np.ascontiguousarray(area),
+    return Mesh(adj=np.array(adj), vol=vol, area=np.ascontiguousarray(area),
                 dist=np.ascontiguousarray(dist), centroid=cen, shape=(nx, ny, nz),
                 size=(Lx, Ly, Lz))
 

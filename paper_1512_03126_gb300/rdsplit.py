@@ -54,6 +54,17 @@ def _declare(L):
         "rdsplit_set_allocator": ([vp, vp, vp], C.c_int),
         "rdsplit_set_timing": ([vp, i32], C.c_int),
         "rdsplit_static_scratch_bytes": ([i32, i32, i32], C.c_size_t),
+        "rdsplit_engine_create": ([i32, i64, C.POINTER(vp)], C.c_int),
+        "rdsplit_engine_set_stream": ([vp, vp], C.c_int),
+        "rdsplit_engine_add": ([vp, vp, dbl, u64, C.POINTER(i32)], C.c_int),
+        "rdsplit_engine_step": ([vp, i64], C.c_int),
+        "rdsplit_engine_poll": ([vp, vp, i32, C.POINTER(i32)], C.c_int),
+        "rdsplit_engine_active": ([vp, C.POINTER(i32), C.POINTER(i64)], C.c_int),
+        "rdsplit_engine_destroy": ([vp], C.c_int),
+        "rdsplit_ensemble_run": ([i32, vp, vp, vp], C.c_int),
+        "rdsplit_engine_set_timing": ([vp, i32], C.c_int),
+        "rdsplit_engine_set_concurrency": ([vp, i32, i32], C.c_int),
+        "rdsplit_engine_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)], C.c_int),
         "rdsplit_run_static": ([i32, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, dbl, vp,
                                 C.POINTER(dbl), C.POINTER(i64), dbl, u64, vp], C.c_int),
         "rdsplit_get_timing": ([vp, C.POINTER(dbl), C.POINTER(i64)], C.c_int),
@@ -199,6 +210,69 @@ def rdsplit_get_timing(h):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().rdsplit_get_timing(h, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def rdsplit_engine_create(max_slots: int, max_active_tets: int):
+    e = C.c_void_p()
+    _check(lib().rdsplit_engine_create(int(max_slots), int(max_active_tets), C.byref(e)))
+    return e
+
+
+def rdsplit_engine_set_stream(e, stream):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(lib().rdsplit_engine_set_stream(e, C.c_void_p(stream or 0)))
+
+
+def rdsplit_engine_add(e, h, t_end: float, seed: int) -> int:
+    slot = C.c_int32()
+    _check(lib().rdsplit_engine_add(e, h, float(t_end), int(seed), C.byref(slot)))
+    return slot.value
+
+
+def rdsplit_engine_step(e, n_steps: int):
+    _check(lib().rdsplit_engine_step(e, int(n_steps)))
+
+
+def rdsplit_engine_poll(e, max_slots: int = 4096):
+    buf = np.zeros(max_slots, np.int32)
+    n = C.c_int32()
+    _check(lib().rdsplit_engine_poll(e, _ptr(buf), int(max_slots), C.byref(n)))
+    return [int(x) for x in buf[:n.value]]
+
+
+def rdsplit_engine_active(e):
+    ns, nt = C.c_int32(), C.c_int64()
+    _check(lib().rdsplit_engine_active(e, C.byref(ns), C.byref(nt)))
+    return ns.value, nt.value
+
+
+def rdsplit_engine_destroy(e):
+    _check(lib().rdsplit_engine_destroy(e))
+
+
+def rdsplit_engine_set_concurrency(e, in_flight: int, cluster: int = 4):
+    _check(lib().rdsplit_engine_set_concurrency(e, int(in_flight), int(cluster)))
+
+
+def rdsplit_engine_set_timing(e, stride: int):
+    _check(lib().rdsplit_engine_set_timing(e, int(stride)))
+
+
+def rdsplit_engine_stats(e):
+    """(global steps, processed entries, sampled ms, sampled launches)."""
+    st, pr, ms, n = C.c_int64(), C.c_int64(), C.c_double(), C.c_int64()
+    _check(lib().rdsplit_engine_stats(e, C.byref(st), C.byref(pr), C.byref(ms), C.byref(n)))
+    return st.value, pr.value, ms.value, n.value
+
+
+def rdsplit_ensemble_run(meshes, t_end, seeds):
+    """Run mesh handles to t_end[i] with seeds[i] in one lockstep engine."""
+    n = len(meshes)
+    hs = (C.c_void_p * n)(*[m.value if hasattr(m, "value") else m for m in meshes])
+    te = np.ascontiguousarray(t_end, np.float64)
+    sd = np.ascontiguousarray(seeds, np.uint64)
+    _check(lib().rdsplit_ensemble_run(n, C.cast(hs, C.c_void_p), _ptr(te), _ptr(sd)))
 
 
 RDSPLIT_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024

@@ -1,0 +1,121 @@
+"""Lockstep engine (batched ensemble and continuous batching) against the
+serial oracle: every simulation in the engine must end with exactly the
+counts the oracle gives it alone (tolerance 0), however it is mixed."""
+import numpy as np
+import pytest
+
+from paper_1512_03126_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1512_03126_gb300 import build
+    build.build()
+    from paper_1512_03126_gb300 import rdsplit
+    return rdsplit
+
+
+def _workloads():
+    out = []
+    for i, n in enumerate([3, 5, 4, 6, 2]):
+        w = I.diffusion_cube(n, 1e-6, 0.2, 40 + i, 6000 if i % 2 == 0 else 7, 0.004 + 0.002 * i, 11 + i)
+        out.append(w)
+    m = I.cube(4, 1e-6, 0.2, 12)
+    nmol = I.molecules(20e-6, 1e-18)
+    out.append(I.Workload("abc_n4", m, I.abc_model(), I.place_by_volume(m, [nmol, nmol, nmol // 3], 4), 2e-3, 7))
+    bar = I.kuhn_box(3, 3, 12, (0.15e-6, 0.15e-6, 0.6e-6), 0.2, 13)
+    V = 0.15e-6 * 0.15e-6 * 0.6e-6
+    f, b = I.molecules(5e-6, V), I.molecules(50e-6, V)
+    out.append(I.Workload("bar_3x3x12", bar, I.bar_model(bar), I.place_by_volume(bar, [f, f, f, b, b, 0, 0, 0], 5),
+                          1.0e-3, 9))
+    for rid in (2, 7, 13):
+        w = I.serving_requests(64)[rid].workload()
+        w.t_end = min(w.t_end, 2e-3)
+        out.append(w)
+    return out
+
+
+def _oracle(oracle, w):
+    return oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed)[0]
+
+
+def test_ensemble_matches_oracle_per_instance(rd, oracle):
+    ws = _workloads()
+    sims = [rd.Simulation(w.mesh, w.model, w.counts) for w in ws]
+    try:
+        rd.rdsplit_ensemble_run([s.h for s in sims], [w.t_end for w in ws], [w.seed for w in ws])
+        for w, s in zip(ws, sims):
+            got = s.counts()
+            assert np.array_equal(got, _oracle(oracle, w)), w.name
+            t, p = s.time
+            assert t == w.t_end
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_continuous_batching_mix_is_invisible(rd, oracle):
+    """Simulations joining at different global steps, with others finishing
+    and their slots reused, each end exactly as when run alone."""
+    ws = _workloads()
+    e = rd.rdsplit_engine_create(3, sum(w.mesh.n_tets for w in ws))
+    sims = {}
+    try:
+        pending = list(range(len(ws)))
+        done = []
+        steps = 0
+        while pending or sims:
+            while pending and len(sims) < 3:
+                i = pending.pop(0)
+                s = rd.Simulation(ws[i].mesh, ws[i].model, ws[i].counts)
+                slot = rd.rdsplit_engine_add(e, s.h, ws[i].t_end, ws[i].seed)
+                sims[slot] = (i, s)
+            rd.rdsplit_engine_step(e, 7 + (steps % 5))
+            steps += 1
+            for slot in rd.rdsplit_engine_poll(e):
+                i, s = sims.pop(slot)
+                done.append((i, s.counts()))
+                s.close()
+        assert len(done) == len(ws)
+        for i, got in done:
+            assert np.array_equal(got, _oracle(oracle, ws[i])), ws[i].name
+    finally:
+        rd.rdsplit_engine_destroy(e)
+        for _, s in sims.values():
+            s.close()
+
+
+def test_engine_admission_limits(rd):
+    w = _workloads()[0]
+    e = rd.rdsplit_engine_create(1, w.mesh.n_tets)
+    a = rd.Simulation(w.mesh, w.model, w.counts)
+    b = rd.Simulation(w.mesh, w.model, w.counts)
+    try:
+        rd.rdsplit_engine_add(e, a.h, w.t_end, 1)
+        with pytest.raises(rd.RdsplitError) as err:
+            rd.rdsplit_engine_add(e, b.h, w.t_end, 1)
+        assert err.value.code == rd.RDSPLIT_ENOMEM
+        rd.rdsplit_engine_step(e, 1 << 30)
+        assert rd.rdsplit_engine_active(e) == (0, 0)
+        assert rd.rdsplit_engine_poll(e) == [0]
+    finally:
+        rd.rdsplit_engine_destroy(e)
+        a.close()
+        b.close()
+
+
+def test_engine_matches_dense_path_after_resume(rd):
+    """A handle advanced first with rdsplit_run_periods and then finished in
+    the engine equals one rdsplit_run."""
+    w = I.diffusion_cube(5, 1e-6, 0.2, 31, 900, 0.03, 17)
+    with rd.Simulation(w.mesh, w.model, w.counts) as a:
+        a.run(w.t_end, w.seed)
+        ref = a.counts()
+    with rd.Simulation(w.mesh, w.model, w.counts) as b:
+        b.run_periods(23, w.seed)
+        rd.rdsplit_ensemble_run([b.h], [w.t_end], [w.seed])
+        assert np.array_equal(b.counts(), ref)

@@ -42,14 +42,15 @@ def test_period_rule_and_alignment(oracle):
     assert t == w.t_end and per == math.ceil(w.t_end / tau)
 
 
-@pytest.mark.parametrize("n0", [6, 300])
+@pytest.mark.parametrize("n0", [6, 300, 6000])
 def test_exact_law_of_pure_diffusion(oracle, n0):
     """With N-bar = N each molecule independently takes one step of the
     period matrix M per period (leave with probability zeta = tau*d, direction
     multinomial by face weight), so the count in tet u after k periods is
     Binomial(N0, (e_src M^k)_u) and the pooled positions are multinomial.
-    n0 = 6 exercises the one-draw-per-molecule path, n0 = 300 the binomial +
-    conditional-binomial path."""
+    n0 = 6 and 300 exercise the one-draw-per-molecule path, n0 = 6000 (above
+    the 4096 cut) the binomial + conditional-binomial path in its first
+    period."""
     m = I.cube(2, 0.5e-6, 0.2, 7)
     model = I.diffusion_model(1e-12)
     c0 = np.zeros((m.n_tets, 1), np.int32)
@@ -58,7 +59,7 @@ def test_exact_law_of_pure_diffusion(oracle, n0):
     tau = oracle.tau(m, model)
     k = 6
     p = np.linalg.matrix_power(one_period_matrix(m, 1e-12, tau), k)[src]
-    seeds = 3000
+    seeds = 3000 if n0 < 1000 else 600
     finals = np.stack([oracle.run(m, model, c0, np.inf, s, max_periods=k)[0][:, 0] for s in range(seeds)])
     assert np.all(finals.sum(1) == n0)
     pooled = finals.sum(0)
@@ -75,7 +76,7 @@ def test_zeta_one_empties_the_fastest_tet(oracle):
     model = I.diffusion_model(1e-12)
     g = np.where(m.adj >= 0, m.area / (m.vol[:, None] * np.where(m.dist > 0, m.dist, 1)), 0).sum(1)
     fast = int(np.nonzero(g == g.max())[0][0])
-    for n0 in (7, 500):
+    for n0 in (7, 500, 5000):
         c0 = np.zeros((m.n_tets, 1), np.int32)
         c0[fast, 0] = n0
         for s in range(20):
