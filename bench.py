@@ -448,6 +448,9 @@ def run_ensemble(args, rank, world, local_rank):
     rd.rdsplit_engine_destroy(eng)
     for s in sims:
         s.close()
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(args, stream)
     if rank != 0:
         return None
     return {
@@ -463,8 +466,54 @@ def run_ensemble(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world} (each rank its own ensemble, own seeds)"},
         "roofline": roofline, "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "serving": serving,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
     }
+
+
+# ----------------------------------------------------------------- serving --
+
+def run_serving(args, stream):
+    """Continuous batching (Poisson arrivals at 200/s, requests drawn from the
+    serving generator, 150 GB device budget): p50/p99 latency and throughput,
+    against the same requests run one after another through rdsplit_run."""
+    import torch
+    from paper_1512_03126_gb300 import inputs as I, serving as SV
+    from paper_1512_03126_gb300 import rdsplit as rd
+    reqs = I.serving_requests(args.requests)
+    t0 = time.perf_counter()
+    prepared = {r.rid: r.workload() for r in reqs}
+    gen_s = time.perf_counter() - t0
+    # warm the path on two small requests
+    small = sorted(reqs, key=lambda r: r.n_tets)[:2]
+    warm = SV.Server(150e9, 8, args.slice, stream=stream)
+    warm.serve([type(r)(r.rid, 0.0, r.n, r.S, r.t_end, r.model_seed) for r in small], prepared)
+    warm.close()
+    dense_stream = torch.cuda.Stream()
+    server = SV.Server(150e9, args.max_slots, args.slice, stream=stream, dense_threshold=args.dense_threshold,
+                       dense_stream=dense_stream)
+    torch.cuda.synchronize()
+    recs = server.serve(reqs, prepared)
+    server.close()
+    torch.cuda.synchronize()
+    out = SV.summarize(recs)
+    # serial plain runs of the same requests
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        w = prepared[r.rid]
+        with rd.Simulation(w.mesh, w.model, w.counts, stream=stream) as sim:
+            sim.run(w.t_end, w.seed)
+            sim.counts()
+    serial_s = time.perf_counter() - t0
+    out.update({"unit": UNIT, "arrival_rate_per_s": 200.0, "budget_gb": 150, "slice_periods": args.slice,
+                "dense_lane_threshold_tet_species": args.dense_threshold,
+                "max_slots": args.max_slots, "serial_plain_s": serial_s,
+                "serial_plain_throughput": out["tet_periods"] / serial_s,
+                "throughput_vs_serial_plain": (out["throughput"] * serial_s / out["tet_periods"]),
+                "request_generation_s": round(gen_s, 1),
+                "latency": "completion - arrival, wall clock, including queueing, upload and read-back"})
+    return out
 
 
 # -------------------------------------------------------------- reference ---
@@ -516,6 +565,12 @@ def main():
     ap.add_argument("--workload", default="ensemble")
     ap.add_argument("--instances", type=int, default=0, help="ensemble: use the first N instances (0 = all 512)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
+    ap.add_argument("--slice", type=int, default=256, help="serving: periods per engine launch")
+    ap.add_argument("--max-slots", type=int, default=64, help="serving: simulations admitted at once")
+    ap.add_argument("--dense-threshold", type=float, default=1e6,
+                    help="serving: n_tets*n_species from which a request runs in the dense lane")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -43,6 +43,8 @@ struct SlotDesc {
     int32_t* N[2];           // count buffers [S][T]; the slice starts in N[0]
     uint8_t* flag[2];        // list membership, by period parity in the slice
     int32_t* list[2];        // active tets, by period parity in the slice
+    const uint4* packed;     // one species: {src, thr} per tet (null: separate arrays)
+    int32_t* N2;             // one species: counts of both parities interleaved (null: N[2])
     uint64_t seed;
     uint32_t period0;        // global period index of local period 0
     int32_t P;               // periods to run in total
@@ -160,6 +162,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         // list when an add to its (zero) next count returns 0; otherwise a
         // byte flag per tet marks list membership.
         const bool by_count = (S == 1) && (d.zero_order == 0u);
+        const bool inter = d.N2 != nullptr;   // interleaved counts (implies by_count)
         uint32_t bad = 0;
         // initial list: occupied tets and tets with a zero-order reaction on
         for (int base = rank * kRunBlock; base < T; base += kC * kRunBlock) {
@@ -168,6 +171,11 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             uint32_t nc = 0;
             if (t < T) {
                 bool occ = kReact && zero_order_on(d, mp, t);
+                if (inter) {
+                    const int32_t c0 = d.N[0][t];
+                    reinterpret_cast<int2*>(d.N2)[t] = make_int2(c0, 0);
+                    occ = occ || c0 > 0;
+                }
                 for (int s = 0; s < S && !occ; ++s) occ = d.N[0][(int64_t)s * T + t] > 0;
                 if (occ && (by_count || set_flag(d.flag[0], t))) cand[nc++] = t;
             }
@@ -181,10 +189,17 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             const bool last = (q == d.P - 1) && d.last_short;
             const double tau_k = last ? d.tau_last : d.tau;
             const float tau_kf = last ? d.tau_lastf : d.tauf;
-            const uint4* thr = last ? d.thr_last : d.thr;
+            // thresholds: packed beside the reverse-face record (stride 2) except
+            // in a shortened last period
+            const bool use_packed = d.packed != nullptr && !last;
+            const uint4* thr = last ? d.thr_last : (use_packed ? d.packed + 1 : d.thr);
+            const int tstride = use_packed ? 2 : 1;
             const uint32_t period = d.period0 + (uint32_t)q;
-            int32_t* Ncur = d.N[r];
-            int32_t* Nnext = d.N[r ^ 1];
+            // counts of this period and the next: N[r] / N[r^1], or the two
+            // halves of the interleaved pairs
+            int32_t* Ncur = inter ? d.N2 + r : d.N[r];
+            int32_t* Nnext = inter ? d.N2 + (r ^ 1) : d.N[r ^ 1];
+            const int64_t cstride = inter ? 2 : 1;
             const int32_t* lcur = d.list[r];
             const bool more = q + 1 < d.q1;
             // kE independent entries per thread and iteration, so that their
@@ -211,31 +226,32 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
 #pragma unroll
                     for (int s = 0; s < SA; ++s) {
                         if (s >= S) break;
-                        N[e][s] = Ncur[(int64_t)s * T + t[e]];
-                        Ncur[(int64_t)s * T + t[e]] = 0;
+                        N[e][s] = Ncur[((int64_t)s * T + t[e]) * cstride];
+                        Ncur[((int64_t)s * T + t[e]) * cstride] = 0;
                     }
                 }
 #pragma unroll
                 for (int e = 0; e < kE; ++e)
                     if (live[e])
                         bad |= step_tet<SA, kReact>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t[e], S, N[e], o[e],
-                                                    &heavy[e], err);
+                                                    &heavy[e], err, tstride);
 #pragma unroll
-                for (int e = 0; e < kE; ++e) warp_split<SA>(heavy[e], d.seed, period, t[e], thr, T, N[e], o[e]);
+                for (int e = 0; e < kE; ++e)
+                    warp_split<SA>(heavy[e], d.seed, period, t[e], thr, T, N[e], o[e], tstride);
 #pragma unroll
                 for (int e = 0; e < kE; ++e) {
                     if (!live[e]) continue;
                     const int tt = t[e];
-                    const int4 sr = d.m.src[tt];
+                    const int4 sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * tt) : d.m.src[tt];
                     const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
                     bool keep = kReact && zero_order_on(d, mp, tt);
                     bool send[4] = {false, false, false, false};
 #pragma unroll
                     for (int s = 0; s < SA; ++s) {
                         if (s >= S) break;
-                        int32_t* Ns = Nnext + (int64_t)s * T;
+                        int32_t* Ns = Nnext + (int64_t)s * T * cstride;
                         if (N[e][s] > 0) {
-                            int32_t old = atomicAdd(Ns + tt, N[e][s]);
+                            int32_t old = atomicAdd(Ns + tt * cstride, N[e][s]);
                             if ((int64_t)old + N[e][s] > 2147483647) bad |= kErrOverflow;
                             if (by_count && old == 0 && more) cand[nc++] = tt;
                             keep = true;
@@ -245,7 +261,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                         for (int f = 0; f < 4; ++f) {
                             if (ov[f] <= 0) continue;
                             if (nbr[f] < 0) { bad |= kErrNegative; continue; }
-                            int32_t old = atomicAdd(Ns + (nbr[f] >> 2), ov[f]);
+                            int32_t old = atomicAdd(Ns + (int64_t)(nbr[f] >> 2) * cstride, ov[f]);
                             if ((int64_t)old + ov[f] > 2147483647) bad |= kErrOverflow;
                             if (by_count && old == 0 && more) cand[nc++] = nbr[f] >> 2;
                             send[f] = true;
@@ -265,12 +281,31 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             // the list just walked is empty for its next use
             if (rank == 0 && threadIdx.x == 0) cnt[r] = 0;
         }
+        if (inter) {
+            // the slice's counts are in the pairs' half (q1 - q0) & 1; hand
+            // them back in N[0] (all adds are complete after the last barrier)
+            const int half = (d.q1 - d.q0) & 1;
+            for (int t = rank * kRunBlock + threadIdx.x; t < T; t += kC * kRunBlock) d.N[0][t] = d.N2[2 * t + half];
+        }
         if (bad) atomicOr(err, bad);
     }
     if (rank == 0 && threadIdx.x == 0) atomicAdd(processed, done);
 }
 
-template <int SA, bool R, int C>
+__global__ void k_pack(int32_t T, const int4* __restrict__ src, const uint4* __restrict__ thr, uint4* __restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int4 s4 = src[t];
+    out[2 * t] = make_uint4((uint32_t)s4.x, (uint32_t)s4.y, (uint32_t)s4.z, (uint32_t)s4.w);
+    out[2 * t + 1] = thr[t];
+}
+
+void launch_pack(int32_t T, const int4* src, const uint4* thr, uint4* out, cudaStream_t st) {
+    k_pack<<<(T + 255) / 256, 256, 0, st>>>(T, src, thr, out);
+    note_launch();
+}
+
+template <int SA, bool R, int C, int E = 1>
 cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParams* mps, const int32_t* order,
                            int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed,
                            cudaStream_t st) {
@@ -286,13 +321,17 @@ cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParam
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C>, descs, mps, order, n_items, head, err, processed);
+    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C, E>, descs, mps, order, n_items, head, err, processed);
 }
 
 template <int SA>
-cudaError_t launch_run_sa(bool react, int cluster, int clusters, const SlotDesc* descs, const ModelParams* mps,
+cudaError_t launch_run_sa(bool react, int cluster, int clusters, int ept, const SlotDesc* descs, const ModelParams* mps,
                           const int32_t* order, int32_t n_items, int32_t* head, uint32_t* err,
                           unsigned long long* processed, cudaStream_t st) {
+    if (SA == 1 && !react && cluster >= 4 && ept >= 4)
+        return launch_cluster<SA, false, 4, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
+    if (SA == 1 && !react && cluster >= 4 && ept == 2)
+        return launch_cluster<SA, false, 4, 2>(clusters, descs, mps, order, n_items, head, err, processed, st);
     if (cluster >= 4) {
         if (react) return launch_cluster<SA, true, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
         return launch_cluster<SA, false, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
@@ -327,6 +366,7 @@ struct rdsplit_engine {
     int sms = 1;
     int32_t concurrency = 0;                  // simulations in flight (0 = default)
     int32_t cluster = 4;                      // CTAs per simulation (1, 2 or 4)
+    int32_t ept = 1;                          // active tets per thread and pass (1, 2 or 4)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
     std::vector<int32_t> slot_q;              // local periods done
@@ -471,6 +511,17 @@ int rdsplit_engine_add(rdsplit_engine_t e, rdsplit_mesh_t h, double t_end, uint6
         return rdapi::fail(RDSPLIT_ECUDA, "%s: memset failed: %s", where, cudaGetErrorString(ce));
     }
     if (last_short) launch_thresholds(h->T, h->mp, h->g, h->G, tau_last, h->thr_last, st);
+    // one species without a zero-order reaction: packed per-tet records and
+    // interleaved counts (fewer cache lines per active tet)
+    bool zero = false;
+    for (int r = 0; r < h->R; ++r) zero = zero || (h->mp.order[r] == 0 && h->mp.k[r] > 0.0);
+    const bool pack = h->S == 1 && !zero && std::isfinite(h->tau);
+    if (pack && !h->packed) {
+        h->packed = (uint4*)rdapi::dev_alloc(32 * T);
+        h->N2 = (int2*)rdapi::dev_alloc(8 * T);
+        if (!h->packed || !h->N2) return rdapi::fail(RDSPLIT_ENOMEM, "%s: packed-record allocation failed", where);
+    }
+    if (pack) launch_pack(h->T, h->src, h->thr, h->packed, st);
     SlotDesc d{};
     d.m = h->dev_mesh();
     d.thr = h->thr;
@@ -481,6 +532,8 @@ int rdsplit_engine_add(rdsplit_engine_t e, rdsplit_mesh_t h, double t_end, uint6
     d.flag[1] = h->flags[1];
     d.list[0] = h->lists[0];
     d.list[1] = h->lists[1];
+    d.packed = pack ? h->packed : nullptr;
+    d.N2 = pack ? reinterpret_cast<int32_t*>(h->N2) : nullptr;
     d.seed = seed;
     d.period0 = (uint32_t)h->period;
     d.P = (int32_t)P;
@@ -563,11 +616,11 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     }
     if (e->timing) cudaEventRecord(e->ev[0], st);
     int32_t* ord = e->d_order;
-    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
     if (e->timing) cudaEventRecord(e->ev[1], st);
     note_launch();
     e->launches += 1;
@@ -590,7 +643,7 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     for (int32_t s : items) {
         SlotDesc& d = e->h_desc[s];
         rdsplit_mesh* h = e->slot_mesh[s];
-        if ((d.q1 - d.q0) & 1) {
+        if (((d.q1 - d.q0) & 1) && !d.N2) {
             std::swap(d.N[0], d.N[1]);
             std::swap(h->cnt, h->rem);
         }
@@ -625,6 +678,13 @@ int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_
         return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_concurrency: bad argument");
     e->concurrency = in_flight;
     e->cluster = cluster;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_set_tets_per_thread(rdsplit_engine_t e, int32_t ept) {
+    if (!e || !(ept == 1 || ept == 2 || ept == 4))
+        return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_tets_per_thread: must be 1, 2 or 4");
+    e->ept = ept;
     return RDSPLIT_OK;
 }
 

@@ -238,7 +238,8 @@ __device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, 
 template <int SA, bool kReact>
 __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams& mp, uint32_t period, double tau_k,
                                              float tau_kf, uint64_t seed, const uint4* __restrict__ thr, int t,
-                                             int S, int32_t* N, int4* o, uint32_t* heavy, uint32_t* err) {
+                                             int S, int32_t* N, int4* o, uint32_t* heavy, uint32_t* err,
+                                             int thr_stride = 1) {
     const int64_t T = m.T;
     uint32_t bad = 0;
     uint32_t touched = 0;
@@ -282,13 +283,14 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
         bool tch = kReact && ((touched >> sp) & 1u);
         if (Nt > 0) {
             if (!tch && Nt < kWarpSplitMin) {
-                x = split_molecules(seed, period, t, sp, Nt, thr[sp * T + t]);
+                x = split_molecules(seed, period, t, sp, Nt, thr[(sp * T + t) * thr_stride]);
             } else if (!tch && Nt < kMoleculeCut) {
                 *heavy |= 1u << sp;        // drawn by the whole warp (warp_split)
                 o[sp] = x;
                 continue;
             } else {
-                x = diffuse(m, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0, thr[sp * T + t]);
+                x = diffuse(m, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
+                            thr[(sp * T + t) * thr_stride]);
             }
         }
         o[sp] = x;
@@ -305,7 +307,8 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
 // of the warp must call this; lanes with heavy == 0 only help.
 template <int SA>
 __device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32_t period, int t,
-                                           const uint4* __restrict__ thr, int64_t T, int32_t* N, int4* o) {
+                                           const uint4* __restrict__ thr, int64_t T, int32_t* N, int4* o,
+                                           int thr_stride = 1) {
     const unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -314,7 +317,7 @@ __device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32
         const int src = __ffs(m) - 1;
         const int my_sp = heavy ? __ffs(heavy) - 1 : 0;
         uint4 myC = make_uint4(0, 0, 0, 0);
-        if (lane == src) myC = thr[my_sp * T + t];
+        if (lane == src) myC = thr[(my_sp * T + t) * thr_stride];
         const int sp = __shfl_sync(kAll, my_sp, src);
         const int32_t n = __shfl_sync(kAll, pick<SA>(N, my_sp), src);
         const int tt = __shfl_sync(kAll, t, src);
