@@ -173,7 +173,8 @@ def run_ours(args, rank, world, local_rank):
     T, S, R = w.mesh.n_tets, w.model.n_species, w.model.n_reactions
     stream = torch.cuda.current_stream()
     sim = rd.Simulation(w.mesh, w.model, stream=stream)
-    seed = w.seed + 1000 * rank
+    from paper_1512_03126_gb300 import dist as D
+    seed = D.rank_seed(w.seed, rank)
     d_init = torch.from_numpy(np.ascontiguousarray(w.counts)).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
@@ -212,9 +213,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = D.max_over_ranks(total_ms, dev)
     seconds = total_ms / 1e3
     value = units_per_step * args.steps * world / seconds
 
@@ -312,9 +311,10 @@ def run_ensemble(args, rank, world, local_rank):
     sizes = I.ensemble_sizes()
     n_inst = len(sizes) if args.instances <= 0 else min(args.instances, len(sizes))
     t0 = time.perf_counter()
-    ws = [I.ensemble_instance(i, int(sizes[i])) for i in range(n_inst)]
+    ws = [I.ensemble_instance(i, int(sizes[i]), args.ensemble_t_end) for i in range(n_inst)]
     gen_s = time.perf_counter() - t0
-    seeds = [w.seed + 100000 * rank for w in ws]
+    from paper_1512_03126_gb300 import dist as D
+    seeds = [D.rank_seed(w.seed, rank) for w in ws]
     sims = [rd.Simulation(w.mesh, w.model, stream=stream) for w in ws]
     inits = [torch.from_numpy(np.ascontiguousarray(w.counts)).to(dev) for w in ws]
     total_tets = sum(w.mesh.n_tets for w in ws)
@@ -371,9 +371,7 @@ def run_ensemble(args, rank, world, local_rank):
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = D.max_over_ranks(total_ms, dev)
     value = units * args.steps * world / (total_ms / 1e3)
     gsteps = (steps1 - steps0) / args.steps
     entries = (proc1 - proc0) / args.steps
@@ -458,7 +456,7 @@ def run_ensemble(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32 counts, f64 rates",
         "data": "synthetic (seeded jittered Kuhn cubes, point-source initial state)",
-        "config": {"workload": f"batched ensemble of {n_inst} cubes n^3*6, n~U{{6..40}}, t_end 0.1 s",
+        "config": {"workload": f"batched ensemble of {n_inst} cubes n^3*6, n~U{{6..40}}, t_end {args.ensemble_t_end} s",
                    "instances": n_inst, "tets": total_tets, "tet_periods_per_step": units,
                    "engine_periods_per_step": gsteps, "periods_sum": sum(periods), "periods_max": max(periods),
                    "processed_entries_per_step": entries, "mesh_generation_s": round(gen_s, 1),
@@ -564,6 +562,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ensemble")
     ap.add_argument("--instances", type=int, default=0, help="ensemble: use the first N instances (0 = all 512)")
+    ap.add_argument("--ensemble-t-end", type=float, default=0.1, help="ensemble: simulated time per instance (s)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")

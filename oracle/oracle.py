@@ -48,6 +48,10 @@ def lib():
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _i32p, C.c_double,
                                    C.c_uint64]
         L.orc_issa_run.restype = C.c_int
+        L.orc_period_tets.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_int32,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, _i32p,
+                                      C.c_int64, C.c_double, C.c_uint64, C.c_int32, C.c_int32, _i32p, _i32p]
+        L.orc_period_tets.restype = C.c_int
         _lib = L
     return _lib
 
@@ -160,3 +164,20 @@ def issa_run(mesh, model, counts, t_end: float, seed: int):
     if rc != 0:
         raise OracleError(f"orc_issa_run failed with code {rc}")
     return c
+
+
+def period_tets(mesh, model, counts, period: int, tau_k: float, seed: int, t_begin: int, t_end: int):
+    """Steps 2-3 of one period for tets t_begin..t_end-1: returns
+    (out [n][S][4], rem [n][S])."""
+    S, R, D, lhs, rhs, k, mask = _model_arrays(model)
+    c = np.ascontiguousarray(counts, np.int32)
+    n = t_end - t_begin
+    out = np.zeros((n, S, 4), np.int32)
+    rem = np.zeros((n, S), np.int32)
+    rc = lib().orc_period_tets(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
+                               lhs.ctypes.data, rhs.ctypes.data, k.ctypes.data, _ptr(mask),
+                               float(model.tau_scale), c, int(period), float(tau_k), int(seed),
+                               int(t_begin), int(t_end), out, rem)
+    if rc != 0:
+        raise OracleError(f"orc_period_tets failed with code {rc}")
+    return out, rem

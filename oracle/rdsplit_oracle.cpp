@@ -31,30 +31,14 @@ const uint32_t kPhiloxM1 = 0xCD9E8D57u;
 const uint32_t kPhiloxW0 = 0x9E3779B9u;   // golden ratio
 const uint32_t kPhiloxW1 = 0xBB67AE85u;   // sqrt(3) - 1
 
-// One Philox4x32 bijection of 10 rounds.  Each round multiplies words 0 and 2
-// by the two constants, keeps high and low halves, and mixes the high halves
-// with words 1 and 3 and the round key; the key is bumped by the Weyl
-// constants between rounds.
-void philox4x32_10(const uint32_t in[4], const uint32_t key[2], uint32_t out[4]) {
-    uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
-    uint32_t k0 = key[0], k1 = key[1];
-    for (int round = 0; round < 10; ++round) {
-        uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)c0;
-        uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)c2;
-        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        uint32_t n1 = (uint32_t)p1;
-        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        uint32_t n3 = (uint32_t)p0;
-        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
-        k0 += kPhiloxW0;
-        k1 += kPhiloxW1;
-    }
-    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+// Full product of two words as (high, low) halves.
+inline void mulhilo(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
 }
 
-// The 64-bit-word member of the same family (Philox4x64-10), used only to pin
-// the round structure above against an independent implementation.
-void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+inline void mulhilo(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
     uint64_t a0 = a & 0xffffffffu, a1 = a >> 32, b0 = b & 0xffffffffu, b1 = b >> 32;
     uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
     uint64_t mid = (p00 >> 32) + (p01 & 0xffffffffu) + (p10 & 0xffffffffu);
@@ -62,19 +46,35 @@ void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
     *hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
 }
 
-void philox4x64_10(const uint64_t in[4], const uint64_t key[2], uint64_t out[4]) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-    uint64_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3], k0 = key[0], k1 = key[1];
+// Ten Philox rounds on a 4-word counter, for 32- or 64-bit words (one code
+// path, so that pinning the 64-bit member against an independent
+// implementation pins the round structure of the 32-bit one).  Each round
+// multiplies words 0 and 2 by the two constants, keeps high and low halves,
+// and mixes the high halves with words 1 and 3 and the round key; the key is
+// bumped by the Weyl constants between rounds.
+template <typename W>
+void philox_rounds(const W in[4], const W key[2], W M0, W M1, W W0, W W1, W out[4]) {
+    W c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3], k0 = key[0], k1 = key[1];
     for (int round = 0; round < 10; ++round) {
-        uint64_t h0, l0, h1, l1;
-        mulhilo64(M0, c0, &h0, &l0);
-        mulhilo64(M1, c2, &h1, &l1);
-        uint64_t n0 = h1 ^ c1 ^ k0, n1 = l1, n2 = h0 ^ c3 ^ k1, n3 = l0;
+        W h0, l0, h1, l1;
+        mulhilo(M0, c0, &h0, &l0);
+        mulhilo(M1, c2, &h1, &l1);
+        W n0 = h1 ^ c1 ^ k0, n1 = l1, n2 = h0 ^ c3 ^ k1, n3 = l0;
         c0 = n0; c1 = n1; c2 = n2; c3 = n3;
-        k0 += W0; k1 += W1;
+        k0 += W0;
+        k1 += W1;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void philox4x32_10(const uint32_t in[4], const uint32_t key[2], uint32_t out[4]) {
+    philox_rounds<uint32_t>(in, key, kPhiloxM0, kPhiloxM1, kPhiloxW0, kPhiloxW1, out);
+}
+
+// The 64-bit-word member of the family (Philox4x64-10).
+void philox4x64_10(const uint64_t in[4], const uint64_t key[2], uint64_t out[4]) {
+    philox_rounds<uint64_t>(in, key, 0xD2E7470EE14C6C93ull, 0xCA5A826395121157ull, 0x9E3779B97F4A7C15ull,
+                            0xBB67AE8584CAA73Bull, out);
 }
 
 enum Purpose : uint32_t { kRounding = 0, kDiffusion = 1, kReaction = 2 };
@@ -579,6 +579,42 @@ int orc_run(int32_t T, const int32_t* adj, const double* vol, const double* area
     for (size_t i = 0; i < N.size(); ++i) counts[i] = (int32_t)N[i];
     *t_io = t_now;
     *period_io = period;
+    return 0;
+}
+
+// Steps 2 and 3 of one period (reactions, then the diffusion draws) for the
+// tets t_begin .. t_end-1 only, from counts [T][S] (only those tets' rows are
+// read).  Writes their out-slots out[(t - t_begin)][S][4] and the molecules
+// that stay, rem[(t - t_begin)][S].  This is the per-process work of the
+// paper's parallel version (Sec. III.D): each process advances its own part
+// of the mesh, then the out-slots on cut faces are exchanged and applied.
+int orc_period_tets(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
+                    int32_t S, const double* D, int32_t R, const int32_t* lhs, const int32_t* rhs,
+                    const double* k, const uint8_t* mask, double tau_scale, const int32_t* counts,
+                    int64_t period, double tau_k, uint64_t seed, int32_t t_begin, int32_t t_end,
+                    int32_t* out, int32_t* rem) {
+    if (T <= 0 || S <= 0 || S > kMaxSpecies || R < 0 || R > kMaxReactions) return -1;
+    if (t_begin < 0 || t_end > T || t_begin > t_end) return -1;
+    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale};
+    Geometry geo = setup_geometry(P);
+    for (int t = t_begin; t < t_end; ++t) {
+        int64_t Nt[kMaxSpecies];
+        double occ[kMaxSpecies], tl[kMaxSpecies];
+        bool touched[kMaxSpecies];
+        for (int s = 0; s < S; ++s) {
+            Nt[s] = counts[(size_t)t * S + s];
+            occ[s] = 0.0; tl[s] = 0.0; touched[s] = false;
+        }
+        react_tet(P, t, (uint32_t)period, tau_k, seed, Nt, occ, tl, touched);
+        for (int s = 0; s < S; ++s) {
+            if (Nt[s] < 0) return -2;
+            int64_t o[4];
+            diffuse_tet_species(P, geo, t, s, (uint32_t)period, tau_k, seed, Nt[s], touched[s], occ[s], o);
+            int64_t sum = 0;
+            for (int f = 0; f < 4; ++f) { out[((size_t)(t - t_begin) * S + s) * 4 + f] = (int32_t)o[f]; sum += o[f]; }
+            rem[(size_t)(t - t_begin) * S + s] = (int32_t)(Nt[s] - sum);
+        }
+    }
     return 0;
 }
 

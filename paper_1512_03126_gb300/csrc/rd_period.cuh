@@ -39,37 +39,69 @@ __device__ __forceinline__ int64_t incoming(const int32_t* __restrict__ op, int4
 // discarded.  Before a species' count changes, its occupancy integral
 // advances by N * (t_event - t_last).
 static __device__ __noinline__ void react_tet(const DevMesh& m, const ModelParams& mp, int t, uint32_t period,
-                                          double tau_k, uint64_t seed, int64_t* N, double* occ, double* tl,
-                                          uint32_t& touched, uint32_t* err) {
-    double avv = kAvogadro * (m.vol[t] * 1000.0);
-    uint32_t on = mp.has_mask ? m.mask[t] : 0xffffffffu;
+                                              double tau_k, uint64_t seed, int64_t* N, double* occ, double* tl,
+                                              uint32_t& touched, uint32_t* err) {
+    const double avv = kAvogadro * (m.vol[t] * 1000.0);
+    const uint32_t on = mp.has_mask ? m.mask[t] : 0xffffffffu;
+    const float2 avf = m.avv[t];
+    // Per-reaction constants of this tet, computed once: the same values as
+    // recomputing them at every event (c = k N_A V, k, or k / (N_A V)).
+    double c[kMaxR];
+    uint32_t cpos = 0;
+    for (int r = 0; r < mp.R; ++r) {
+        double kr = mp.k[r];
+        int o = mp.order[r];
+        c[r] = ((on >> r) & 1u) ? (o == 0 ? kr * avv : (o == 1 ? kr : kr / avv)) : 0.0;
+        if (c[r] > 0.0) cpos |= 1u << r;
+    }
     rdd::Stream st(seed, (uint32_t)t, period, rdd::kPurposeReaction, 0);
     double tc = 0.0;
     int events = 0;
     for (;;) {
+        // propensity a_r = c_r h_r, h_r the number of reactant combinations
+        int64_t h[kMaxR];
+        bool any = false;
+        for (int r = 0; r < mp.R; ++r) {
+            int64_t hr = 1;
+            int a1 = mp.rs1[r], a2 = mp.rs2[r];
+            if (a1 >= 0) {
+                if (a2 < 0) hr = N[a1];
+                else if (a1 == a2) hr = N[a1] * (N[a1] - 1) / 2;
+                else hr = N[a1] * N[a2];
+            }
+            h[r] = hr;
+            any = any || (((cpos >> r) & 1u) && hr != 0);
+        }
+        if (!any) break;                       // a0 = 0
+        const uint64_t x53 = st.bits53();
+        // After an event, a single-precision bound often proves that the
+        // next event time tc - log(u1)/a0 reaches tau_k (see surely_no_event;
+        // here the span is tau_k - tc, kept well above rounding by the
+        // 1e-9 guard), which skips the double-precision log and divide.
+        if (events > 0) {
+            const double span = tau_k - tc;
+            if (span > tau_k * 1e-9) {
+                float a0f = 0.0f;
+                for (int r = 0; r < mp.R; ++r) {
+                    if (!((cpos >> r) & 1u) || h[r] == 0) continue;
+                    int o = mp.order[r];
+                    float cf = o == 0 ? mp.kf[r] * avf.x : (o == 1 ? mp.kf[r] : mp.kf[r] * avf.y);
+                    a0f += cf * (float)h[r];
+                }
+                const uint64_t y = 9007199254740991ull - x53;
+                const uint32_t yhi = (uint32_t)(y >> 29);
+                const float need = a0f * (float)span * 1.0001f;
+                if (yhi != 0u && need < 3.0e38f && (float)yhi * 5.9604644775390625e-08f >= need) break;
+            }
+        }
         double a[kMaxR];
         double a0 = 0.0;
         for (int r = 0; r < mp.R; ++r) {
-            double ar = 0.0;
-            if ((on >> r) & 1u) {
-                int64_t h = 1;
-                for (int s = 0; s < mp.S; ++s) {
-                    int nu = mp.lhs[r][s];
-                    if (nu == 1) h = h * N[s];
-                    else if (nu == 2) h = h * (N[s] * (N[s] - 1) / 2);
-                }
-                if (h != 0) {
-                    double kr = mp.k[r];
-                    int o = mp.order[r];
-                    double c = o == 0 ? kr * avv : (o == 1 ? kr : kr / avv);
-                    ar = c * (double)h;
-                }
-            }
+            double ar = c[r] * (double)h[r];
             a[r] = ar;
             a0 = a0 + ar;
         }
-        if (!(a0 > 0.0)) break;
-        double u1 = st.u01_open0();
+        const double u1 = ((double)x53 + 1.0) * (1.0 / 9007199254740992.0);
         double tn = tc + (-rdd::own_log(u1)) / a0;
         if (tn >= tau_k) break;
         double target = st.u01() * a0;
@@ -362,5 +394,6 @@ __device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32
         }
     }
 }
+
 
 }  // namespace rdk
