@@ -47,11 +47,12 @@ PROFILES = os.path.join(ROOT, "profiles")
 # --------------------------------------------------------------- workloads --
 
 def engine_bytes_per_entry(S: int) -> int:
-    """Bytes the lockstep engine must move per processed (slot, tet) entry:
-    the list entry (8), the reverse-face table (16), one list append and its
-    flag (10) and, per species, the count read and clear (8), the thresholds
-    (16), the kept-count add (4) and the four face adds (16)."""
-    return 34 + 44 * S
+    """Bytes the batched engine must move per processed (slot, tet) entry:
+    the reverse-face record (16), the next-period bitmap bit (one 4-byte
+    word update) and, per species, the count read and clear (8), the
+    thresholds (16), the kept-count add (4) and the four face adds (16).  The
+    bitmap scan (8 bytes per 32 tets and period) is not counted."""
+    return 20 + 44 * S
 
 
 def make_workload(name: str):
@@ -298,7 +299,7 @@ def cpu_baseline(w, seconds: float):
 
 def run_ensemble(args, rank, world, local_rank):
     """512 independent simulations (n^3*6 jittered cubes, n ~ U{6..40}), each
-    run from its initial state to t_end = 0.1 s: batched in the lockstep
+    run from its initial state to t_end = 0.1 s: batched in the persistent
     engine (one launch per global step for all of them) against the plain
     form (each simulation's own launch sequence through rdsplit_run)."""
     import torch

@@ -197,10 +197,6 @@ int rdsplit_engine_destroy(rdsplit_engine_t engine);
  * 4; default 4) that share its work through distributed shared memory.
  * Fewer in flight keeps their working sets in L2. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
-/* Active tets each thread handles per pass (1, 2 or 4; used for one-species
- * simulations without reactions on clusters of 4): more overlap their memory
- * round trips at the cost of registers. */
-int rdsplit_engine_set_tets_per_thread(rdsplit_engine_t engine, int32_t tets_per_thread);
 /* Profiling: time every engine launch with CUDA events (on != 0), and read
  * the periods advanced (maximum per step call, summed), the (simulation, tet)
  * entries processed, and the summed milliseconds / number of timed launches. */

@@ -35,8 +35,7 @@ struct rdsplit_mesh {
     uint4* thr = nullptr;
     uint4* thr_last = nullptr;
     int32_t* staging = nullptr;
-    uint8_t* flags[2] = {nullptr, nullptr};   // active-list membership (batched engine)
-    int32_t* lists[2] = {nullptr, nullptr};   // active tets (batched engine)
+    uint32_t* bits[2] = {nullptr, nullptr};   // active-tet bitmaps by period parity (batched engine)
     uint4* packed = nullptr;   // one species: {reverse-face record, thresholds} per tet (batched engine)
     int2* N2 = nullptr;        // one species: {count, count} of two period parities (batched engine)
     rdk::ModelParams mp{};
@@ -64,7 +63,7 @@ struct rdsplit_mesh {
     ~rdsplit_mesh() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         free_model();
-        void* ps[] = {src, g, G, vol, gmax, err, flags[0], flags[1], lists[0], lists[1], packed, N2};
+        void* ps[] = {src, g, G, vol, gmax, err, bits[0], bits[1], packed, N2};
         for (void* p : ps) rdapi::dev_free(p);
     }
 };

@@ -2,19 +2,18 @@
 // persistent kernel, touching only tets that hold molecules.
 //
 // Realisations run in parallel are the embarrassingly parallel use of the
-// method (Sec. I of arXiv:1512.03126).  Each thread block takes one
+// method (Sec. I of arXiv:1512.03126).  Each thread-block cluster takes one
 // simulation from a work queue (largest first) and runs its periods of
-// Algorithm 1 itself, with __syncthreads() as the period barrier, so that
-// no grid-wide synchronisation and no spin-wait is needed.  Per period the
-// block walks the simulation's list of tets that hold molecules (or have a
-// zero-order reaction on), runs the same per-tet work as the dense kernel
-// (step_tet, warp_split), and adds the molecules that stay or leave into the
-// next count buffer with integer atomic adds — exact and independent of
-// order, so the counts equal those of the dense gather.  A tet enters the
-// next list on the 0 -> 1 transition of its flag (or, with one species, of
-// its next count), so it appears once; the list counter lives in shared
-// memory.  One simulation's active region is
-// touched by one SM only, which keeps it in that SM's L1 and in L2.
+// Algorithm 1 itself, with cluster.sync() as the period barrier, so that no
+// grid-wide synchronisation and no spin-wait is needed.  Per period the
+// cluster visits the tets whose bit is set in that period's activity bitmap
+// (tets that hold molecules or have a zero-order reaction on), runs the same
+// per-tet work as the dense kernel (step_tet, warp_split), and adds the
+// molecules that stay or leave into the next count buffer with integer atomic
+// adds — exact and independent of order, so the counts equal those of the
+// dense gather.  A tet that keeps or receives molecules sets its bit in the
+// next period's bitmap.  One simulation's active region is touched by one
+// cluster only, which keeps it in those SMs' L1 and in L2.
 //
 // The random streams of a simulation are keyed by its own seed, period index
 // and canonical tet ids, so its counts do not depend on what runs beside it.
@@ -41,8 +40,7 @@ struct SlotDesc {
     const uint4* thr;        // thresholds for tau
     const uint4* thr_last;   // thresholds for the shortened last period
     int32_t* N[2];           // count buffers [S][T]; the slice starts in N[0]
-    uint8_t* flag[2];        // list membership, by period parity in the slice
-    int32_t* list[2];        // active tets, by period parity in the slice
+    uint32_t* bits[2];       // active-tet bitmaps (bit t of word t/32), by period parity in the slice
     const uint4* packed;     // one species: {src, thr} per tet (null: separate arrays)
     int32_t* N2;             // one species: counts of both parities interleaved (null: N[2])
     uint64_t seed;
@@ -56,97 +54,74 @@ struct SlotDesc {
     float tauf, tau_lastf;
 };
 
-// Flags are bytes; set one with an atomic OR on its 32-bit word.
-__device__ __forceinline__ bool set_flag(uint8_t* flags, int t) {
-    unsigned int* w = reinterpret_cast<unsigned int*>(flags + (t & ~3));
-    unsigned int bit = 1u << (8 * (t & 3));
-    unsigned int old = atomicOr(w, bit);
-    return (old & bit) == 0u;
-}
-
 __device__ __forceinline__ bool zero_order_on(const SlotDesc& d, const ModelParams& mp, int t) {
     if (!d.zero_order) return false;
     uint32_t on = mp.has_mask ? d.m.mask[t] : 0xffffffffu;
     return (on & d.zero_order) != 0u;
 }
 
-// Block-wide exclusive prefix sum of small per-thread counts; *total gets
-// the block sum.  Every thread of the block must call it.
-__device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t* total, uint32_t* warp_sums) {
-    constexpr int kWarps = kRunBlock / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t v = x;
+// Position of the k-th (0-based) set bit of w; w has more than k set bits.
+__device__ __forceinline__ int select_bit(uint32_t w, uint32_t k) {
+    int pos = 0;
 #pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, v, dd);
-        if (lane >= dd) v += y;
-    }
-    if (lane == 31) warp_sums[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < kWarps ? warp_sums[lane] : 0u;
-#pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, dd);
-            if (lane >= dd) w += y;
+    for (int half = 16; half > 0; half >>= 1) {
+        const uint32_t low = (uint32_t)__popc(w & ((1u << half) - 1u));
+        if (k >= low) {
+            k -= low;
+            w >>= half;
+            pos += half;
         }
-        if (lane < kWarps) warp_sums[lane] = w;
     }
-    __syncthreads();
-    uint32_t before = (warp > 0 ? warp_sums[warp - 1] : 0u) + v - x;
-    *total = warp_sums[kWarps - 1];
-    __syncthreads();   // warp_sums is reused by the next call
-    return before;
+    return pos;
 }
 
-// Append each thread's candidates to `list`: one atomic add per CTA on the
-// list counter *cnt, which lives in the shared memory of the cluster's first
-// CTA (a distributed-shared-memory address when the cluster has several).
-__device__ __forceinline__ void block_append(const int* cand, uint32_t ncand, int32_t* list, uint32_t capacity,
-                                             uint32_t* cnt, uint32_t* warp_sums, uint32_t* block_base,
-                                             uint32_t& bad) {
-    uint32_t total = 0;
-    uint32_t off = block_scan(ncand, &total, warp_sums);
-    if (threadIdx.x == 0) *block_base = total ? atomicAdd(cnt, total) : 0u;
-    __syncthreads();
-    const uint32_t base = *block_base;
-    for (uint32_t k = 0; k < ncand; ++k) {
-        uint32_t pos = base + off + k;
-        if (pos < capacity) list[pos] = cand[k];
-        else bad |= kErrOverflow;
+// The lane whose word holds the warp's j-th active tet, given each lane's
+// exclusive prefix `before` of the set-bit counts (non-decreasing over the
+// lanes): the largest lane with before <= j.  Every lane must call it.
+__device__ __forceinline__ int owner_lane(uint32_t before, uint32_t j) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t b = __shfl_sync(0xffffffffu, before, lo + step);
+        if (b <= j) lo += step;
     }
-    __syncthreads();
+    return lo;
 }
 
 // One simulation per cluster of kC CTAs (kC = 1: per CTA).  The cluster's
-// first CTA owns the work-item index and the list counters; the others read
-// and update them through distributed shared memory.  cluster.sync() (a
-// hardware barrier) separates periods.
-template <int SA, bool kReact, int kC, int kE = 1>
+// first CTA owns the work-item index; the others read it through distributed
+// shared memory.  cluster.sync() (a hardware barrier) separates periods.
+//
+// The tets to visit in a period are the set bits of that period's bitmap.
+// Warp g of the cluster's kW warps reads words g, g + kW, g + 2 kW, ... (one
+// per lane, 32 kW words per pass), so the active tets of a dense region are
+// spread over all warps, and the tets a warp visits together lie in 32-tet
+// runs of the mesh numbering.  Each visited word is cleared for its next use;
+// a tet that keeps or receives molecules sets its bit in the other parity's
+// bitmap (an atomic OR, which is idempotent, so no membership test and no
+// list are needed).  At the end of a slice both bitmaps are zero.
+template <int SA, bool kReact, int kC>
 __global__ void __launch_bounds__(kRunBlock, (SA <= 1 && !kReact) ? 2 : 1)
 k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__ mps, const int32_t* __restrict__ order,
              int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed) {
     namespace cg = cooperative_groups;
+    constexpr unsigned kAll = 0xffffffffu;
+    constexpr int kWarps = kRunBlock / 32;
+    constexpr int kW = kC * kWarps;   // warps per simulation
     __shared__ int32_t item_s;
-    __shared__ uint32_t cnt_s[2];
-    __shared__ uint32_t warp_sums[kRunBlock / 32];
-    __shared__ uint32_t block_base;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
     int32_t* item = kC > 1 ? cluster.map_shared_rank(&item_s, 0) : &item_s;
-    uint32_t* cnt = kC > 1 ? cluster.map_shared_rank(&cnt_s[0], 0) : &cnt_s[0];
     auto csync = [&]() {
         if (kC > 1) cluster.sync();
         else __syncthreads();
     };
+    const int lane = threadIdx.x & 31;
+    const int gw = rank * kWarps + (threadIdx.x >> 5);
     unsigned long long done = 0;
     for (;;) {
         csync();
-        if (rank == 0 && threadIdx.x == 0) {
-            *item = atomicAdd(head, 1);
-            cnt[0] = 0;
-            cnt[1] = 0;
-        }
+        if (rank == 0 && threadIdx.x == 0) *item = atomicAdd(head, 1);
         csync();
         const int32_t k = *item;
         // every CTA has read the item before the leader may overwrite it or
@@ -158,34 +133,29 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         const ModelParams& mp = mps[slot];
         const int T = d.m.T;
         const int S = d.S;
-        // With one species and no zero-order reaction, a tet joins the next
-        // list when an add to its (zero) next count returns 0; otherwise a
-        // byte flag per tet marks list membership.
-        const bool by_count = (S == 1) && (d.zero_order == 0u);
-        const bool inter = d.N2 != nullptr;   // interleaved counts (implies by_count)
+        const int W = (T + 31) >> 5;
+        const bool inter = d.N2 != nullptr;   // one species, interleaved counts
         uint32_t bad = 0;
-        // initial list: occupied tets and tets with a zero-order reaction on
-        for (int base = rank * kRunBlock; base < T; base += kC * kRunBlock) {
+        // initial bitmap: occupied tets and tets with a zero-order reaction on
+        // (whole words, written by the first lane of each 32-tet run)
+        for (int base = rank * kRunBlock; base < W * 32; base += kC * kRunBlock) {
             const int t = base + threadIdx.x;
-            int cand[1];
-            uint32_t nc = 0;
+            bool occ = false;
             if (t < T) {
-                bool occ = kReact && zero_order_on(d, mp, t);
+                occ = kReact && zero_order_on(d, mp, t);
                 if (inter) {
                     const int32_t c0 = d.N[0][t];
                     reinterpret_cast<int2*>(d.N2)[t] = make_int2(c0, 0);
                     occ = occ || c0 > 0;
                 }
                 for (int s = 0; s < S && !occ; ++s) occ = d.N[0][(int64_t)s * T + t] > 0;
-                if (occ && (by_count || set_flag(d.flag[0], t))) cand[nc++] = t;
             }
-            block_append(cand, nc, d.list[0], (uint32_t)T, &cnt[0], warp_sums, &block_base, bad);
+            const uint32_t word = __ballot_sync(kAll, occ);
+            if (lane == 0) d.bits[0][t >> 5] = word;
         }
         for (int q = d.q0; q < d.q1; ++q) {
             const int r = (q - d.q0) & 1;
-            csync();   // the previous period's appends are complete
-            const uint32_t n = cnt[r];
-            if (rank == 0) done += n;
+            csync();   // the previous period's adds and bits are complete
             const bool last = (q == d.P - 1) && d.last_short;
             const double tau_k = last ? d.tau_last : d.tau;
             const float tau_kf = last ? d.tau_lastf : d.tauf;
@@ -200,96 +170,96 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             int32_t* Ncur = inter ? d.N2 + r : d.N[r];
             int32_t* Nnext = inter ? d.N2 + (r ^ 1) : d.N[r ^ 1];
             const int64_t cstride = inter ? 2 : 1;
-            const int32_t* lcur = d.list[r];
+            uint32_t* bcur = d.bits[r];
+            uint32_t* bnext = d.bits[r ^ 1];
             const bool more = q + 1 < d.q1;
-            // kE independent entries per thread and iteration, so that their
-            // memory round trips overlap
-            for (uint32_t base = (uint32_t)rank * kRunBlock * kE; base < n; base += kC * kRunBlock * kE) {
-                int cand[5 * kE];
-                uint32_t nc = 0;
-                int t[kE];
-                bool live[kE];
-                uint32_t heavy[kE];
-                int32_t N[kE][SA];
-                int4 o[kE][SA];
-#pragma unroll
-                for (int e = 0; e < kE; ++e) {
-                    const uint32_t i = base + e * kRunBlock + threadIdx.x;
-                    live[e] = i < n;
-                    t[e] = live[e] ? lcur[i] : 0;
-                    heavy[e] = 0;
+            for (int w0 = 0; w0 < W; w0 += 32 * kW) {
+                const int wi = w0 + lane * kW + gw;
+                uint32_t word = 0;
+                if (wi < W) {
+                    word = bcur[wi];
+                    if (word) bcur[wi] = 0u;
                 }
+                const uint32_t c = (uint32_t)__popc(word);
+                uint32_t inc = c;
 #pragma unroll
-                for (int e = 0; e < kE; ++e) {
-                    if (!live[e]) continue;
-                    if (!by_count) d.flag[r][t[e]] = 0;
+                for (int dd = 1; dd < 32; dd <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kAll, inc, dd);
+                    if (lane >= dd) inc += y;
+                }
+                const uint32_t total = __shfl_sync(kAll, inc, 31);
+                const uint32_t before = inc - c;
+                done += total;
+                for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+                    const uint32_t j = j0 + (uint32_t)lane;
+                    const bool live = j < total;
+                    const uint32_t jj = live ? j : total - 1u;
+                    const int own = owner_lane(before, jj);
+                    const uint32_t own_word = __shfl_sync(kAll, word, own);
+                    const uint32_t own_before = __shfl_sync(kAll, before, own);
+                    const int t = live ? (w0 + own * kW + gw) * 32 + select_bit(own_word, jj - own_before) : 0;
+                    uint32_t heavy = 0;
+                    int32_t N[SA];
+                    int4 o[SA];
+                    if (live) {
 #pragma unroll
-                    for (int s = 0; s < SA; ++s) {
-                        if (s >= S) break;
-                        N[e][s] = Ncur[((int64_t)s * T + t[e]) * cstride];
-                        Ncur[((int64_t)s * T + t[e]) * cstride] = 0;
+                        for (int s = 0; s < SA; ++s) {
+                            if (s >= S) break;
+                            int32_t* p = Ncur + ((int64_t)s * T + t) * cstride;
+                            N[s] = *p;
+                            *p = 0;
+                        }
+                        bad |= step_tet<SA, kReact>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o, &heavy,
+                                                    err, tstride);
                     }
-                }
-#pragma unroll
-                for (int e = 0; e < kE; ++e)
-                    if (live[e])
-                        bad |= step_tet<SA, kReact>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t[e], S, N[e], o[e],
-                                                    &heavy[e], err, tstride);
-#pragma unroll
-                for (int e = 0; e < kE; ++e)
-                    warp_split<SA>(heavy[e], d.seed, period, t[e], thr, T, N[e], o[e], tstride);
-#pragma unroll
-                for (int e = 0; e < kE; ++e) {
-                    if (!live[e]) continue;
-                    const int tt = t[e];
-                    const int4 sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * tt) : d.m.src[tt];
+                    warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride);
+                    if (!live) continue;
+                    const int4 sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
                     const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
-                    bool keep = kReact && zero_order_on(d, mp, tt);
+                    bool keep = kReact && zero_order_on(d, mp, t);
                     bool send[4] = {false, false, false, false};
 #pragma unroll
                     for (int s = 0; s < SA; ++s) {
                         if (s >= S) break;
                         int32_t* Ns = Nnext + (int64_t)s * T * cstride;
-                        if (N[e][s] > 0) {
-                            int32_t old = atomicAdd(Ns + tt * cstride, N[e][s]);
-                            if ((int64_t)old + N[e][s] > 2147483647) bad |= kErrOverflow;
-                            if (by_count && old == 0 && more) cand[nc++] = tt;
+                        if (N[s] > 0) {
+                            const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
+                            if (old > 2147483647 - N[s]) bad |= kErrOverflow;
                             keep = true;
                         }
-                        const int ov[4] = {o[e][s].x, o[e][s].y, o[e][s].z, o[e][s].w};
+                        const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
 #pragma unroll
                         for (int f = 0; f < 4; ++f) {
                             if (ov[f] <= 0) continue;
                             if (nbr[f] < 0) { bad |= kErrNegative; continue; }
-                            int32_t old = atomicAdd(Ns + (int64_t)(nbr[f] >> 2) * cstride, ov[f]);
-                            if ((int64_t)old + ov[f] > 2147483647) bad |= kErrOverflow;
-                            if (by_count && old == 0 && more) cand[nc++] = nbr[f] >> 2;
+                            const int32_t old = atomicAdd(Ns + (int64_t)(nbr[f] >> 2) * cstride, ov[f]);
+                            if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
                             send[f] = true;
                         }
                     }
-                    if (more && !by_count) {
-                        uint8_t* fl = d.flag[r ^ 1];
-                        if (keep && set_flag(fl, tt)) cand[nc++] = tt;
+                    if (more) {
+                        if (keep) atomicOr(bnext + (t >> 5), 1u << (t & 31));
 #pragma unroll
-                        for (int f = 0; f < 4; ++f)
-                            if (send[f] && set_flag(fl, nbr[f] >> 2)) cand[nc++] = nbr[f] >> 2;
+                        for (int f = 0; f < 4; ++f) {
+                            if (!send[f]) continue;
+                            const int u = nbr[f] >> 2;
+                            atomicOr(bnext + (u >> 5), 1u << (u & 31));
+                        }
                     }
                 }
-                block_append(cand, nc, d.list[r ^ 1], (uint32_t)T, &cnt[r ^ 1], warp_sums, &block_base, bad);
             }
-            csync();   // every CTA has read cnt[r] and finished the period
-            // the list just walked is empty for its next use
-            if (rank == 0 && threadIdx.x == 0) cnt[r] = 0;
         }
+        csync();   // every add of the slice is complete
         if (inter) {
             // the slice's counts are in the pairs' half (q1 - q0) & 1; hand
-            // them back in N[0] (all adds are complete after the last barrier)
+            // them back in N[0]
             const int half = (d.q1 - d.q0) & 1;
             for (int t = rank * kRunBlock + threadIdx.x; t < T; t += kC * kRunBlock) d.N[0][t] = d.N2[2 * t + half];
         }
         if (bad) atomicOr(err, bad);
     }
-    if (rank == 0 && threadIdx.x == 0) atomicAdd(processed, done);
+    // entries processed: counted by lane 0 of each warp (total is warp-uniform)
+    if (lane == 0 && done) atomicAdd(processed, done);
 }
 
 __global__ void k_pack(int32_t T, const int4* __restrict__ src, const uint4* __restrict__ thr, uint4* __restrict__ out) {
@@ -305,7 +275,7 @@ void launch_pack(int32_t T, const int4* src, const uint4* thr, uint4* out, cudaS
     note_launch();
 }
 
-template <int SA, bool R, int C, int E = 1>
+template <int SA, bool R, int C>
 cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParams* mps, const int32_t* order,
                            int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed,
                            cudaStream_t st) {
@@ -321,17 +291,13 @@ cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParam
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C, E>, descs, mps, order, n_items, head, err, processed);
+    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C>, descs, mps, order, n_items, head, err, processed);
 }
 
 template <int SA>
-cudaError_t launch_run_sa(bool react, int cluster, int clusters, int ept, const SlotDesc* descs, const ModelParams* mps,
+cudaError_t launch_run_sa(bool react, int cluster, int clusters, const SlotDesc* descs, const ModelParams* mps,
                           const int32_t* order, int32_t n_items, int32_t* head, uint32_t* err,
                           unsigned long long* processed, cudaStream_t st) {
-    if (SA == 1 && !react && cluster >= 4 && ept >= 4)
-        return launch_cluster<SA, false, 4, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
-    if (SA == 1 && !react && cluster >= 4 && ept == 2)
-        return launch_cluster<SA, false, 4, 2>(clusters, descs, mps, order, n_items, head, err, processed, st);
     if (cluster >= 4) {
         if (react) return launch_cluster<SA, true, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
         return launch_cluster<SA, false, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
@@ -366,7 +332,6 @@ struct rdsplit_engine {
     int sms = 1;
     int32_t concurrency = 0;                  // simulations in flight (0 = default)
     int32_t cluster = 4;                      // CTAs per simulation (1, 2 or 4)
-    int32_t ept = 1;                          // active tets per thread and pass (1, 2 or 4)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
     std::vector<int32_t> slot_q;              // local periods done
@@ -394,7 +359,7 @@ int engine_err(rdsplit_engine* e, const char* where) {
     }
     if (v == 0) return RDSPLIT_OK;
     cudaMemsetAsync(e->err, 0, sizeof(uint32_t), e->stream);
-    if (v & kErrOverflow) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: count overflow or active-list capacity exceeded", where);
+    if (v & kErrOverflow) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: count overflow", where);
     if (v & kErrEventCap) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: SSA event cap exceeded", where);
     if (v & kErrNegative) return rdapi::fail(RDSPLIT_EINVAL, "%s: negative count", where);
     return rdapi::fail(RDSPLIT_ECUDA, "%s: device error bits 0x%x", where, v);
@@ -494,17 +459,15 @@ int rdsplit_engine_add(rdsplit_engine_t e, rdsplit_mesh_t h, double t_end, uint6
     if (h->period + P > (int64_t)0xffffffffll) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: period index exceeds 2^32-1", where);
     if (P > 0x7fffffffll) return rdapi::fail(RDSPLIT_EINVAL, "%s: too many periods", where);
     const size_t T = (size_t)h->T;
-    if (!h->flags[0]) {
-        h->flags[0] = (uint8_t*)rdapi::dev_alloc(T + 4);
-        h->flags[1] = (uint8_t*)rdapi::dev_alloc(T + 4);
-        h->lists[0] = (int32_t*)rdapi::dev_alloc(4 * T);
-        h->lists[1] = (int32_t*)rdapi::dev_alloc(4 * T);
-        if (!h->flags[0] || !h->flags[1] || !h->lists[0] || !h->lists[1])
-            return rdapi::fail(RDSPLIT_ENOMEM, "%s: list allocation failed", where);
+    const size_t W = (T + 31) / 32;
+    if (!h->bits[0]) {
+        h->bits[0] = (uint32_t*)rdapi::dev_alloc(4 * W);
+        h->bits[1] = (uint32_t*)rdapi::dev_alloc(4 * W);
+        if (!h->bits[0] || !h->bits[1]) return rdapi::fail(RDSPLIT_ENOMEM, "%s: bitmap allocation failed", where);
     }
     cudaStream_t st = e->stream;
-    cudaError_t ce = cudaMemsetAsync(h->flags[0], 0, T + 4, st);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->flags[1], 0, T + 4, st);
+    cudaError_t ce = cudaMemsetAsync(h->bits[0], 0, 4 * W, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->bits[1], 0, 4 * W, st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->rem, 0, sizeof(int32_t) * T * h->S, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
@@ -528,10 +491,8 @@ int rdsplit_engine_add(rdsplit_engine_t e, rdsplit_mesh_t h, double t_end, uint6
     d.thr_last = last_short ? h->thr_last : h->thr;
     d.N[0] = h->cnt;
     d.N[1] = h->rem;
-    d.flag[0] = h->flags[0];
-    d.flag[1] = h->flags[1];
-    d.list[0] = h->lists[0];
-    d.list[1] = h->lists[1];
+    d.bits[0] = h->bits[0];
+    d.bits[1] = h->bits[1];
     d.packed = pack ? h->packed : nullptr;
     d.N2 = pack ? reinterpret_cast<int32_t*>(h->N2) : nullptr;
     d.seed = seed;
@@ -616,11 +577,11 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     }
     if (e->timing) cudaEventRecord(e->ev[0], st);
     int32_t* ord = e->d_order;
-    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->ept, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
     if (e->timing) cudaEventRecord(e->ev[1], st);
     note_launch();
     e->launches += 1;
@@ -678,13 +639,6 @@ int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_
         return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_concurrency: bad argument");
     e->concurrency = in_flight;
     e->cluster = cluster;
-    return RDSPLIT_OK;
-}
-
-int rdsplit_engine_set_tets_per_thread(rdsplit_engine_t e, int32_t ept) {
-    if (!e || !(ept == 1 || ept == 2 || ept == 4))
-        return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_tets_per_thread: must be 1, 2 or 4");
-    e->ept = ept;
     return RDSPLIT_OK;
 }
 

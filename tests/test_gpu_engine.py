@@ -119,3 +119,59 @@ def test_engine_matches_dense_path_after_resume(rd):
         b.run_periods(23, w.seed)
         rd.rdsplit_ensemble_run([b.h], [w.t_end], [w.seed])
         assert np.array_equal(b.counts(), ref)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("in_flight", [1, 3])
+def test_every_cluster_shape_matches_oracle(rd, oracle, cluster, in_flight):
+    """The engine's result does not depend on how many CTAs share a
+    simulation or how many simulations run at once."""
+    ws = _workloads()
+    sims = [rd.Simulation(w.mesh, w.model, w.counts) for w in ws]
+    e = rd.rdsplit_engine_create(len(ws), sum(w.mesh.n_tets for w in ws))
+    try:
+        rd.rdsplit_engine_set_concurrency(e, in_flight, cluster)
+        for w, s in zip(ws, sims):
+            rd.rdsplit_engine_add(e, s.h, w.t_end, w.seed)
+        rd.rdsplit_engine_step(e, 1 << 30)
+        assert sorted(rd.rdsplit_engine_poll(e, 64)) == list(range(len(ws)))
+        for w, s in zip(ws, sims):
+            assert np.array_equal(s.counts(), _oracle(oracle, w)), (w.name, cluster, in_flight)
+    finally:
+        rd.rdsplit_engine_destroy(e)
+        for s in sims:
+            s.close()
+
+
+def test_full_size_ensemble_and_requests_in_one_launch(rd):
+    """Every stored full-size oracle run of an ensemble instance or a serving
+    request (tests/golden/oracle_runs.json, written from the oracle alone),
+    all advanced together by one persistent engine launch in the default
+    launch configuration, ends with the oracle's counts (SHA-256 of the final
+    counts, period index and per-species totals)."""
+    import hashlib
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_runs.json")
+    recs = {k: v for k, v in json.load(open(path)).items()
+            if v["kind"] in ("ensemble", "request") and v["max_periods"] < 0}
+    assert len(recs) >= 40
+    ws, names = [], []
+    for name, rec in sorted(recs.items()):
+        a = rec["args"]
+        ws.append(I.ensemble_instance(a["i"], a["n"]) if rec["kind"] == "ensemble"
+                  else I.serving_requests(64)[a["rid"]].workload())
+        names.append(name)
+    sims = [rd.Simulation(w.mesh, w.model, w.counts) for w in ws]
+    try:
+        rd.rdsplit_ensemble_run([s.h for s in sims], [w.t_end for w in ws], [w.seed for w in ws])
+        for name, w, s in zip(names, ws, sims):
+            rec = recs[name]
+            g = s.counts()
+            t, p = s.time
+            assert p == rec["period"], name
+            assert [int(x) for x in g.sum(0)] == rec["totals"], name
+            assert hashlib.sha256(np.ascontiguousarray(g, dtype="<i4").tobytes()).hexdigest() == rec["sha256"], name
+    finally:
+        for s in sims:
+            s.close()
