@@ -300,8 +300,8 @@ def cpu_baseline(w, seconds: float):
 def run_ensemble(args, rank, world, local_rank):
     """512 independent simulations (n^3*6 jittered cubes, n ~ U{6..40}), each
     run from its initial state to t_end = 0.1 s: batched in the persistent
-    engine (one launch per global step for all of them) against the plain
-    form (each simulation's own launch sequence through rdsplit_run)."""
+    engine (one launch for all of them) against the plain form (each
+    simulation's own launch sequence through rdsplit_run)."""
     import torch
     from paper_1512_03126_gb300 import build, inputs as I
     build.build()

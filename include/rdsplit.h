@@ -197,6 +197,11 @@ int rdsplit_engine_destroy(rdsplit_engine_t engine);
  * 4; default 4) that share its work through distributed shared memory.
  * Fewer in flight keeps their working sets in L2. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
+/* Activity bitmaps (one bit per tet and period parity) are kept in the
+ * distributed shared memory of a simulation's cluster when both fit in
+ * `max_bytes` per CTA (0 ..= 163840; default 163840), else in global memory.
+ * 0 forces global bitmaps.  Results do not depend on this setting. */
+int rdsplit_engine_set_bitmap_smem(rdsplit_engine_t engine, int32_t max_bytes);
 /* Profiling: time every engine launch with CUDA events (on != 0), and read
  * the periods advanced (maximum per step call, summed), the (simulation, tet)
  * entries processed, and the summed milliseconds / number of timed launches. */

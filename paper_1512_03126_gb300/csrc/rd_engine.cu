@@ -88,40 +88,73 @@ __device__ __forceinline__ int owner_lane(uint32_t before, uint32_t j) {
     return lo;
 }
 
+constexpr int kGroup = 8;        // bitmap words per lane loaded at once
+constexpr int kRowStride = 136;  // shared bitmap words per row: 16 warps x 8, padded against bank conflicts
+constexpr int kMaxSharedBitsBytes = 160 * 1024;
+
+// Shared-memory words (both parities) a simulation of W bitmap words needs
+// on each CTA of a cluster of kc CTAs.
+inline int64_t shared_bits_words(int64_t W, int kc) {
+    const int64_t kw = (int64_t)kc * (kRunBlock / 32);
+    const int64_t rows = (W + 8 * kw - 1) / (8 * kw);
+    return 2 * rows * kRowStride;
+}
+
 // One simulation per cluster of kC CTAs (kC = 1: per CTA).  The cluster's
 // first CTA owns the work-item index; the others read it through distributed
 // shared memory.  cluster.sync() (a hardware barrier) separates periods.
 //
 // The tets to visit in a period are the set bits of that period's bitmap.
-// Warp g of the cluster's kW warps reads words g, g + kW, g + 2 kW, ... (one
-// per lane, 32 kW words per pass), so the active tets of a dense region are
-// spread over all warps, and the tets a warp visits together lie in 32-tet
-// runs of the mesh numbering.  Each visited word is cleared for its next use;
-// a tet that keeps or receives molecules sets its bit in the other parity's
-// bitmap (an atomic OR, which is idempotent, so no membership test and no
-// list are needed).  At the end of a slice both bitmaps are zero.
+// The words are dealt to the cluster's kW warps in runs of 8 (256 tets, one
+// 32-byte sector): run r of a group goes to warp r mod kW, so the active tets
+// of a dense region are spread over all warps, and each lane loads kGroup
+// words at once.  The warp hands the set bits of its 32 x kGroup words to its
+// lanes, 32 at a time, by a prefix sum of the lanes' popcounts, an owner-lane
+// search and a select-the-k-th-bit step.  Each visited word is cleared for
+// its next use; a tet that keeps or receives molecules sets its bit in the
+// other parity's bitmap (an atomic OR, which is idempotent, so no membership
+// test and no list are needed).  At the end of a slice both bitmaps are zero.
+//
+// The bitmaps live in distributed shared memory when they fit (both parities
+// in kMaxSharedBitsBytes per CTA): the run of 8 words that warp g scans is
+// kept in the shared memory of warp g's CTA, so the scan reads local shared
+// memory and the bit sets are shared-memory atomics on the owning CTA, with
+// no L2 traffic.  Larger simulations use the global bitmaps.
+//
+// Count adds return the old value to detect a count above 2^31-1, except in
+// a simulation without reactions whose molecules sum to at most 2^31-1: no
+// count can overflow there, and the adds need not wait for a reply.
 template <int SA, bool kReact, int kC>
-__global__ void __launch_bounds__(kRunBlock, (SA <= 1 && !kReact) ? 2 : 1)
+__global__ void __launch_bounds__(kRunBlock, 1)
 k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__ mps, const int32_t* __restrict__ order,
-             int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed) {
+             int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed, int32_t dyn_words) {
     namespace cg = cooperative_groups;
     constexpr unsigned kAll = 0xffffffffu;
     constexpr int kWarps = kRunBlock / 32;
     constexpr int kW = kC * kWarps;   // warps per simulation
     __shared__ int32_t item_s;
+    __shared__ uint32_t total_s[2];   // molecules of a reaction-free simulation; [1] != 0: above 2^31-1
+    __shared__ uint32_t wbuf[kWarps][kGroup * 32];
+    extern __shared__ uint32_t sbits[];   // [2][rows * kRowStride]: this CTA's runs of both bitmaps
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
     int32_t* item = kC > 1 ? cluster.map_shared_rank(&item_s, 0) : &item_s;
+    uint32_t* total = kC > 1 ? cluster.map_shared_rank(&total_s[0], 0) : &total_s[0];
     auto csync = [&]() {
         if (kC > 1) cluster.sync();
         else __syncthreads();
     };
     const int lane = threadIdx.x & 31;
     const int gw = rank * kWarps + (threadIdx.x >> 5);
+    uint32_t* wb = wbuf[threadIdx.x >> 5];
     unsigned long long done = 0;
     for (;;) {
         csync();
-        if (rank == 0 && threadIdx.x == 0) *item = atomicAdd(head, 1);
+        if (rank == 0 && threadIdx.x == 0) {
+            *item = atomicAdd(head, 1);
+            total[0] = 0u;
+            total[1] = 0u;
+        }
         csync();
         const int32_t k = *item;
         // every CTA has read the item before the leader may overwrite it or
@@ -129,33 +162,64 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         csync();
         if (k >= n_items) break;
         const int slot = order[k];
-        const SlotDesc d = descs[slot];
+        const SlotDesc& d = descs[slot];   // read-only; fields are loaded where used
         const ModelParams& mp = mps[slot];
         const int T = d.m.T;
         const int S = d.S;
         const int W = (T + 31) >> 5;
         const bool inter = d.N2 != nullptr;   // one species, interleaved counts
+        const bool conserved = mp.R == 0;     // molecules are only moved
+        const int rw = (W + 8 * kW - 1) / (8 * kW) * kRowStride;
+        const bool in_smem = 2 * rw <= dyn_words;
+        // word wi of bitmap p: in the shared memory of the CTA whose warp
+        // scans it, or in global memory
+        auto word_ptr = [&](int p, int wi) -> uint32_t* {
+            if (!in_smem) return d.bits[p] + wi;
+            const int run = wi >> 3;
+            const int owner = run % kW;
+            uint32_t* a = sbits + p * rw + (run / kW) * kRowStride + (owner % kWarps) * 8 + (wi & 7);
+            if (kC == 1) return a;
+            return cluster.map_shared_rank(a, owner / kWarps);
+        };
         uint32_t bad = 0;
+        if (in_smem)
+            for (int i = threadIdx.x; i < rw; i += kRunBlock) sbits[rw + i] = 0u;   // bitmap 1 starts empty
         // initial bitmap: occupied tets and tets with a zero-order reaction on
-        // (whole words, written by the first lane of each 32-tet run)
+        // (whole words, written by the first lane of each 32-tet run); and the
+        // molecule total of a reaction-free simulation
+        unsigned long long mine = 0;
         for (int base = rank * kRunBlock; base < W * 32; base += kC * kRunBlock) {
             const int t = base + threadIdx.x;
             bool occ = false;
             if (t < T) {
                 occ = kReact && zero_order_on(d, mp, t);
-                if (inter) {
-                    const int32_t c0 = d.N[0][t];
-                    reinterpret_cast<int2*>(d.N2)[t] = make_int2(c0, 0);
-                    occ = occ || c0 > 0;
+                for (int s = 0; s < S; ++s) {
+                    const int32_t c = d.N[0][(int64_t)s * T + t];
+                    occ = occ || c > 0;
+                    mine += (uint32_t)max(c, 0);
+                    if (inter) reinterpret_cast<int2*>(d.N2)[t] = make_int2(c, 0);
                 }
-                for (int s = 0; s < S && !occ; ++s) occ = d.N[0][(int64_t)s * T + t] > 0;
             }
             const uint32_t word = __ballot_sync(kAll, occ);
-            if (lane == 0) d.bits[0][t >> 5] = word;
+            if (lane == 0 && (t >> 5) < W) *word_ptr(0, t >> 5) = word;
         }
+        if (conserved) {
+#pragma unroll
+            for (int dd = 16; dd > 0; dd >>= 1) mine += __shfl_xor_sync(kAll, mine, dd);
+            if (lane == 0 && mine) {
+                if (mine > 2147483647ull) {
+                    atomicOr(&total[1], 1u);
+                } else {
+                    const uint32_t old = atomicAdd(&total[0], (uint32_t)mine);
+                    if ((unsigned long long)old + mine > 2147483647ull) atomicOr(&total[1], 1u);
+                }
+            }
+        }
+        bool exact = true;
         for (int q = d.q0; q < d.q1; ++q) {
             const int r = (q - d.q0) & 1;
             csync();   // the previous period's adds and bits are complete
+            if (q == d.q0) exact = !conserved || total[1] != 0u;
             const bool last = (q == d.P - 1) && d.last_short;
             const double tau_k = last ? d.tau_last : d.tau;
             const float tau_kf = last ? d.tau_lastf : d.tauf;
@@ -170,38 +234,73 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             int32_t* Ncur = inter ? d.N2 + r : d.N[r];
             int32_t* Nnext = inter ? d.N2 + (r ^ 1) : d.N[r ^ 1];
             const int64_t cstride = inter ? 2 : 1;
-            uint32_t* bcur = d.bits[r];
-            uint32_t* bnext = d.bits[r ^ 1];
+            // this warp's runs of the current bitmap (row stride kRowStride in
+            // shared memory) or the global bitmap
+            uint32_t* bcur = in_smem ? sbits + r * rw + (threadIdx.x >> 5) * 8 : d.bits[r];
             const bool more = q + 1 < d.q1;
-            for (int w0 = 0; w0 < W; w0 += 32 * kW) {
-                const int wi = w0 + lane * kW + gw;
-                uint32_t word = 0;
-                if (wi < W) {
-                    word = bcur[wi];
-                    if (word) bcur[wi] = 0u;
+            for (int g0 = 0; g0 < W; g0 += kGroup * 32 * kW) {
+                uint32_t wds[kGroup];
+#pragma unroll
+                for (int kk = 0; kk < kGroup; ++kk) {
+                    const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
+                    const int li = in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
+                    wds[kk] = wi < W ? bcur[li] : 0u;
                 }
-                const uint32_t c = (uint32_t)__popc(word);
+                uint32_t c = 0;
+#pragma unroll
+                for (int kk = 0; kk < kGroup; ++kk) {
+                    const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
+                    const int li = in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
+                    if (wds[kk]) bcur[li] = 0u;
+                    wb[kk * 32 + lane] = wds[kk];
+                    c += (uint32_t)__popc(wds[kk]);
+                }
+                __syncwarp();
                 uint32_t inc = c;
 #pragma unroll
                 for (int dd = 1; dd < 32; dd <<= 1) {
                     const uint32_t y = __shfl_up_sync(kAll, inc, dd);
                     if (lane >= dd) inc += y;
                 }
-                const uint32_t total = __shfl_sync(kAll, inc, 31);
+                const uint32_t n_act = __shfl_sync(kAll, inc, 31);
                 const uint32_t before = inc - c;
-                done += total;
-                for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+                done += n_act;
+                for (uint32_t j0 = 0; j0 < n_act; j0 += 32) {
                     const uint32_t j = j0 + (uint32_t)lane;
-                    const bool live = j < total;
-                    const uint32_t jj = live ? j : total - 1u;
+                    const bool live = j < n_act;
+                    const uint32_t jj = live ? j : n_act - 1u;
                     const int own = owner_lane(before, jj);
-                    const uint32_t own_word = __shfl_sync(kAll, word, own);
-                    const uint32_t own_before = __shfl_sync(kAll, before, own);
-                    const int t = live ? (w0 + own * kW + gw) * 32 + select_bit(own_word, jj - own_before) : 0;
+                    uint32_t rel = jj - __shfl_sync(kAll, before, own);
+                    // the owner's word that holds bit number rel
+                    int kw = 0;
+                    uint32_t ww = 0;
+                    bool found = false;
+#pragma unroll
+                    for (int kk = 0; kk < kGroup; ++kk) {
+                        const uint32_t w = wb[kk * 32 + own];
+                        const uint32_t pc = (uint32_t)__popc(w);
+                        if (!found) {
+                            if (rel < pc) {
+                                found = true;
+                                kw = kk;
+                                ww = w;
+                            } else {
+                                rel -= pc;
+                            }
+                        }
+                    }
+                    const int t = live ? (g0 + ((kw * 4 + (own >> 3)) * kW + gw) * 8 + (own & 7)) * 32 +
+                                             select_bit(ww, rel)
+                                       : 0;
                     uint32_t heavy = 0;
                     int32_t N[SA];
                     int4 o[SA];
+                    int4 sr = make_int4(-1, -1, -1, -1);
+                    uint4 pre = make_uint4(0u, 0u, 0u, 0u);
                     if (live) {
+                        // the tet's record and counts, loaded together
+                        sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
+                        if (use_packed) pre = d.packed[2 * t + 1];
 #pragma unroll
                         for (int s = 0; s < SA; ++s) {
                             if (s >= S) break;
@@ -210,11 +309,10 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                             *p = 0;
                         }
                         bad |= step_tet<SA, kReact>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o, &heavy,
-                                                    err, tstride);
+                                                    err, tstride, use_packed, pre);
                     }
-                    warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride);
+                    warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride, use_packed, pre);
                     if (!live) continue;
-                    const int4 sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
                     const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
                     bool keep = kReact && zero_order_on(d, mp, t);
                     bool send[4] = {false, false, false, false};
@@ -223,8 +321,12 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                         if (s >= S) break;
                         int32_t* Ns = Nnext + (int64_t)s * T * cstride;
                         if (N[s] > 0) {
-                            const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
-                            if (old > 2147483647 - N[s]) bad |= kErrOverflow;
+                            if (exact) {
+                                const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
+                                if (old > 2147483647 - N[s]) bad |= kErrOverflow;
+                            } else {
+                                atomicAdd(Ns + (int64_t)t * cstride, N[s]);
+                            }
                             keep = true;
                         }
                         const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
@@ -232,21 +334,27 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                         for (int f = 0; f < 4; ++f) {
                             if (ov[f] <= 0) continue;
                             if (nbr[f] < 0) { bad |= kErrNegative; continue; }
-                            const int32_t old = atomicAdd(Ns + (int64_t)(nbr[f] >> 2) * cstride, ov[f]);
-                            if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
+                            int32_t* dst = Ns + (int64_t)(nbr[f] >> 2) * cstride;
+                            if (exact) {
+                                const int32_t old = atomicAdd(dst, ov[f]);
+                                if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
+                            } else {
+                                atomicAdd(dst, ov[f]);
+                            }
                             send[f] = true;
                         }
                     }
                     if (more) {
-                        if (keep) atomicOr(bnext + (t >> 5), 1u << (t & 31));
+                        if (keep) atomicOr(word_ptr(r ^ 1, t >> 5), 1u << (t & 31));
 #pragma unroll
                         for (int f = 0; f < 4; ++f) {
                             if (!send[f]) continue;
                             const int u = nbr[f] >> 2;
-                            atomicOr(bnext + (u >> 5), 1u << (u & 31));
+                            atomicOr(word_ptr(r ^ 1, u >> 5), 1u << (u & 31));
                         }
                     }
                 }
+                __syncwarp();   // wb is rewritten by the next group
             }
         }
         csync();   // every add of the slice is complete
@@ -258,7 +366,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         }
         if (bad) atomicOr(err, bad);
     }
-    // entries processed: counted by lane 0 of each warp (total is warp-uniform)
+    // entries processed: counted by lane 0 of each warp (n_act is warp-uniform)
     if (lane == 0 && done) atomicAdd(processed, done);
 }
 
@@ -278,11 +386,19 @@ void launch_pack(int32_t T, const int4* src, const uint4* thr, uint4* out, cudaS
 template <int SA, bool R, int C>
 cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParams* mps, const int32_t* order,
                            int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed,
-                           cudaStream_t st) {
+                           int32_t dyn_words, cudaStream_t st) {
+    cudaError_t ce = cudaFuncSetAttribute(k_engine_run<SA, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kMaxSharedBitsBytes);
+    if (ce != cudaSuccess) return ce;
+    if (C == 1) {
+        k_engine_run<SA, R, C><<<clusters, kRunBlock, (size_t)dyn_words * 4, st>>>(descs, mps, order, n_items, head,
+                                                                                  err, processed, dyn_words);
+        return cudaGetLastError();
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(clusters * C, 1, 1);
     cfg.blockDim = dim3(kRunBlock, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = (size_t)dyn_words * 4;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -291,24 +407,24 @@ cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParam
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C>, descs, mps, order, n_items, head, err, processed);
+    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C>, descs, mps, order, n_items, head, err, processed,
+                              dyn_words);
 }
 
 template <int SA>
 cudaError_t launch_run_sa(bool react, int cluster, int clusters, const SlotDesc* descs, const ModelParams* mps,
                           const int32_t* order, int32_t n_items, int32_t* head, uint32_t* err,
-                          unsigned long long* processed, cudaStream_t st) {
+                          unsigned long long* processed, int32_t dyn_words, cudaStream_t st) {
     if (cluster >= 4) {
-        if (react) return launch_cluster<SA, true, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
-        return launch_cluster<SA, false, 4>(clusters, descs, mps, order, n_items, head, err, processed, st);
+        if (react) return launch_cluster<SA, true, 4>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
+        return launch_cluster<SA, false, 4>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
     }
     if (cluster == 2) {
-        if (react) return launch_cluster<SA, true, 2>(clusters, descs, mps, order, n_items, head, err, processed, st);
-        return launch_cluster<SA, false, 2>(clusters, descs, mps, order, n_items, head, err, processed, st);
+        if (react) return launch_cluster<SA, true, 2>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
+        return launch_cluster<SA, false, 2>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
     }
-    if (react) k_engine_run<SA, true, 1><<<clusters, kRunBlock, 0, st>>>(descs, mps, order, n_items, head, err, processed);
-    else k_engine_run<SA, false, 1><<<clusters, kRunBlock, 0, st>>>(descs, mps, order, n_items, head, err, processed);
-    return cudaGetLastError();
+    if (react) return launch_cluster<SA, true, 1>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
+    return launch_cluster<SA, false, 1>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
 }
 
 }  // namespace
@@ -332,6 +448,7 @@ struct rdsplit_engine {
     int sms = 1;
     int32_t concurrency = 0;                  // simulations in flight (0 = default)
     int32_t cluster = 4;                      // CTAs per simulation (1, 2 or 4)
+    int32_t bitmap_smem = kMaxSharedBitsBytes;  // shared memory per CTA for activity bitmaps (0: global only)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
     std::vector<int32_t> slot_q;              // local periods done
@@ -567,9 +684,16 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     }
     const int n_items = (int)order.size();
     const int csize = e->cluster;
-    // default: about one simulation per 4.75 SMs (32 on 152), which keeps the
-    // simulations' scattered working sets within L2 (measured optimum)
-    const int in_flight = e->concurrency > 0 ? e->concurrency : std::max(1, (e->sms * 4) / 19);
+    // shared-memory bitmaps: room for the largest simulation that fits
+    int64_t dyn_words = 0;
+    for (int32_t s : items) {
+        const int64_t need = shared_bits_words((e->slot_mesh[s]->T + 31) / 32, csize);
+        if (need * 4 <= e->bitmap_smem) dyn_words = std::max(dyn_words, need);
+    }
+    // default: one CTA per SM (38 clusters of 4 on 152 SMs).  More
+    // simulations in flight than that spill their scattered working sets out
+    // of L2 (152 one-CTA simulations run 25% slower than 38 four-CTA ones).
+    const int in_flight = e->concurrency > 0 ? e->concurrency : std::max(1, e->sms / std::max(1, csize));
     const int clusters = std::min(n_items, in_flight);
     if (e->timing && !e->ev[0]) {
         cudaEventCreate(&e->ev[0]);
@@ -577,11 +701,11 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     }
     if (e->timing) cudaEventRecord(e->ev[0], st);
     int32_t* ord = e->d_order;
-    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
-    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, st);
+    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
+    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
+    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
+    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
+    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
     if (e->timing) cudaEventRecord(e->ev[1], st);
     note_launch();
     e->launches += 1;
@@ -639,6 +763,14 @@ int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_
         return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_concurrency: bad argument");
     e->concurrency = in_flight;
     e->cluster = cluster;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_set_bitmap_smem(rdsplit_engine_t e, int32_t max_bytes) {
+    if (!e || max_bytes < 0 || max_bytes > kMaxSharedBitsBytes)
+        return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_bitmap_smem: max_bytes must be in [0, %d]",
+                           kMaxSharedBitsBytes);
+    e->bitmap_smem = max_bytes;
     return RDSPLIT_OK;
 }
 

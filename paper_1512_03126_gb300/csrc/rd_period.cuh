@@ -37,13 +37,14 @@ __device__ __forceinline__ int64_t incoming(const int32_t* __restrict__ op, int4
 // Reaction phase of one tet (Algorithm 1, Step 2 and 2.1): Gillespie's
 // direct method over [0, tau_k); the first event at or past tau_k is
 // discarded.  Before a species' count changes, its occupancy integral
-// advances by N * (t_event - t_last).
-static __device__ __noinline__ void react_tet(const DevMesh& m, const ModelParams& mp, int t, uint32_t period,
-                                              double tau_k, uint64_t seed, int64_t* N, double* occ, double* tl,
-                                              uint32_t& touched, uint32_t* err) {
-    const double avv = kAvogadro * (m.vol[t] * 1000.0);
-    const uint32_t on = mp.has_mask ? m.mask[t] : 0xffffffffu;
-    const float2 avf = m.avv[t];
+// advances by N * (t_event - t_last).  The tet's volume, reaction mask and
+// single-precision (N_A V, 1/(N_A V)) come in by value: a non-inlined
+// function that took the mesh by reference would pin the caller's copy of
+// it in local memory.
+static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint32_t period, double tau_k,
+                                              uint64_t seed, double vol_t, uint32_t on, float2 avf, int64_t* N,
+                                              double* occ, double* tl, uint32_t& touched, uint32_t* err) {
+    const double avv = kAvogadro * (vol_t * 1000.0);
     // Per-reaction constants of this tet, computed once: the same values as
     // recomputing them at every event (c = k N_A V, k, or k / (N_A V)).
     double c[kMaxR];
@@ -135,10 +136,11 @@ static __device__ __noinline__ void react_tet(const DevMesh& m, const ModelParam
 // count changed during the period, else N), n = min(Binomial(N*, zeta), N),
 // split over the faces by conditional binomials; below N* = kMoleculeCut the
 // same law one molecule at a time against the cumulative thresholds.
-static __device__ __noinline__ int4 diffuse(const DevMesh& m, int t, int s, double Dsp, uint32_t period, double tau_k,
-                                        uint64_t seed, int64_t Nt, bool touched, double occ, uint4 C) {
+static __device__ __noinline__ int4 diffuse(const double* __restrict__ G, const double* __restrict__ gface, int t,
+                                            int s, double Dsp, uint32_t period, double tau_k, uint64_t seed,
+                                            int64_t Nt, bool touched, double occ, uint4 C) {
     int4 o = make_int4(0, 0, 0, 0);
-    double Gt = m.G[t];
+    double Gt = G[t];
     double z = zeta_of(tau_k, Dsp, Gt);
     if (!(z > 0.0) || Nt <= 0) return o;
     int64_t Nstar = Nt;
@@ -167,7 +169,7 @@ static __device__ __noinline__ int4 diffuse(const DevMesh& m, int t, int s, doub
     if (n > Nt) n = Nt;
     if (n == 0) return o;
     double g[4];
-    for (int f = 0; f < 4; ++f) g[f] = m.g[4 * t + f];
+    for (int f = 0; f < 4; ++f) g[f] = gface[4 * t + f];
     double suf[4];
     double acc = 0.0;
     for (int f = 3; f >= 0; --f) { acc = g[f] + acc; suf[f] = acc; }
@@ -266,12 +268,13 @@ __device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, 
 // stay and o[s] the molecules leaving through each face, except for the
 // species whose bit is set in *heavy: those (untouched, 10 <= N < 4096) are
 // left for warp_split, which the whole warp must call next.  Returns error
-// bits.
+// bits.  With has_pre, `pre` holds species 0's thresholds, already loaded.
 template <int SA, bool kReact>
 __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams& mp, uint32_t period, double tau_k,
                                              float tau_kf, uint64_t seed, const uint4* __restrict__ thr, int t,
                                              int S, int32_t* N, int4* o, uint32_t* heavy, uint32_t* err,
-                                             int thr_stride = 1) {
+                                             int thr_stride = 1, bool has_pre = false,
+                                             uint4 pre = make_uint4(0u, 0u, 0u, 0u)) {
     const int64_t T = m.T;
     uint32_t bad = 0;
     uint32_t touched = 0;
@@ -296,7 +299,8 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
                 occ[sp] = 0.0;
                 tl[sp] = 0.0;
             }
-            react_tet(m, mp, t, period, tau_k, seed, N64, occ, tl, touched, err);
+            react_tet(mp, t, period, tau_k, seed, m.vol[t], mp.has_mask ? m.mask[t] : 0xffffffffu, m.avv[t], N64, occ,
+                      tl, touched, err);
 #pragma unroll
             for (int sp = 0; sp < SA; ++sp) {
                 if (sp >= S) break;
@@ -315,14 +319,14 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
         bool tch = kReact && ((touched >> sp) & 1u);
         if (Nt > 0) {
             if (!tch && Nt < kWarpSplitMin) {
-                x = split_molecules(seed, period, t, sp, Nt, thr[(sp * T + t) * thr_stride]);
+                x = split_molecules(seed, period, t, sp, Nt, (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
             } else if (!tch && Nt < kMoleculeCut) {
                 *heavy |= 1u << sp;        // drawn by the whole warp (warp_split)
                 o[sp] = x;
                 continue;
             } else {
-                x = diffuse(m, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
-                            thr[(sp * T + t) * thr_stride]);
+                x = diffuse(m.G, m.g, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
+                            (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
             }
         }
         o[sp] = x;
@@ -336,11 +340,13 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
 // computes Philox blocks l, l+32, ... of the tet's diffusion stream (block b
 // holds the uniforms of molecules 4b..4b+3, exactly the words the sequential
 // draw would use) and the face counts are summed over the warp.  Every lane
-// of the warp must call this; lanes with heavy == 0 only help.
+// of the warp must call this; lanes with heavy == 0 only help.  With has_pre,
+// `pre` holds the calling lane's species-0 thresholds, already loaded.
 template <int SA>
 __device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32_t period, int t,
                                            const uint4* __restrict__ thr, int64_t T, int32_t* N, int4* o,
-                                           int thr_stride = 1) {
+                                           int thr_stride = 1, bool has_pre = false,
+                                           uint4 pre = make_uint4(0u, 0u, 0u, 0u)) {
     const unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -349,7 +355,7 @@ __device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32
         const int src = __ffs(m) - 1;
         const int my_sp = heavy ? __ffs(heavy) - 1 : 0;
         uint4 myC = make_uint4(0, 0, 0, 0);
-        if (lane == src) myC = thr[(my_sp * T + t) * thr_stride];
+        if (lane == src) myC = (has_pre && my_sp == 0) ? pre : thr[(my_sp * T + t) * thr_stride];
         const int sp = __shfl_sync(kAll, my_sp, src);
         const int32_t n = __shfl_sync(kAll, pick<SA>(N, my_sp), src);
         const int tt = __shfl_sync(kAll, t, src);

@@ -64,6 +64,7 @@ def _declare(L):
         "rdsplit_ensemble_run": ([i32, vp, vp, vp], C.c_int),
         "rdsplit_engine_set_timing": ([vp, i32], C.c_int),
         "rdsplit_engine_set_concurrency": ([vp, i32, i32], C.c_int),
+        "rdsplit_engine_set_bitmap_smem": ([vp, i32], C.c_int),
         "rdsplit_engine_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)], C.c_int),
         "rdsplit_run_static": ([i32, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, dbl, vp,
                                 C.POINTER(dbl), C.POINTER(i64), dbl, u64, vp], C.c_int),
@@ -253,6 +254,10 @@ def rdsplit_engine_destroy(e):
 
 def rdsplit_engine_set_concurrency(e, in_flight: int, cluster: int = 4):
     _check(lib().rdsplit_engine_set_concurrency(e, int(in_flight), int(cluster)))
+
+
+def rdsplit_engine_set_bitmap_smem(e, max_bytes: int):
+    _check(lib().rdsplit_engine_set_bitmap_smem(e, int(max_bytes)))
 
 
 def rdsplit_engine_set_timing(e, stride: int):

@@ -121,22 +121,30 @@ def test_engine_matches_dense_path_after_resume(rd):
         assert np.array_equal(b.counts(), ref)
 
 
+@pytest.fixture(scope="module")
+def oracle_results(oracle):
+    return [_oracle(oracle, w) for w in _workloads()]
+
+
 @pytest.mark.parametrize("cluster", [1, 2, 4])
 @pytest.mark.parametrize("in_flight", [1, 3])
-def test_every_cluster_shape_matches_oracle(rd, oracle, cluster, in_flight):
+@pytest.mark.parametrize("bitmap_smem", [0, 160 * 1024])
+def test_every_cluster_shape_matches_oracle(rd, oracle_results, cluster, in_flight, bitmap_smem):
     """The engine's result does not depend on how many CTAs share a
-    simulation or how many simulations run at once."""
+    simulation, how many simulations run at once, or where the activity
+    bitmaps live (global memory, or the cluster's shared memory)."""
     ws = _workloads()
     sims = [rd.Simulation(w.mesh, w.model, w.counts) for w in ws]
     e = rd.rdsplit_engine_create(len(ws), sum(w.mesh.n_tets for w in ws))
     try:
         rd.rdsplit_engine_set_concurrency(e, in_flight, cluster)
+        rd.rdsplit_engine_set_bitmap_smem(e, bitmap_smem)
         for w, s in zip(ws, sims):
             rd.rdsplit_engine_add(e, s.h, w.t_end, w.seed)
         rd.rdsplit_engine_step(e, 1 << 30)
         assert sorted(rd.rdsplit_engine_poll(e, 64)) == list(range(len(ws)))
-        for w, s in zip(ws, sims):
-            assert np.array_equal(s.counts(), _oracle(oracle, w)), (w.name, cluster, in_flight)
+        for w, s, ref in zip(ws, sims, oracle_results):
+            assert np.array_equal(s.counts(), ref), (w.name, cluster, in_flight, bitmap_smem)
     finally:
         rd.rdsplit_engine_destroy(e)
         for s in sims:
