@@ -84,10 +84,11 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per launch of the period kernel from a committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(PROFILES, f"k_period_{workload}.md")
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
+    summary (profiles/<kernel>_<workload>.md), if it was taken on the
+    current kernel source."""
+    path = os.path.join(PROFILES, f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -224,7 +225,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = bpt * T / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     roofline = {"kernel": "k_period", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("k_period", args.workload),
                 "bytes_per_tet_period": bpt, "launch_us": round(per_launch_s * 1e6, 3),
                 "sampled_launches": kn, "peak_source": f"{peak_kind} hbm_gbs"}
 
@@ -381,8 +382,8 @@ def run_ensemble(args, rank, world, local_rank):
     launches_per_step = kn / args.steps if args.steps else 1
     achieved = bpe * (entries / launches_per_step) / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    roofline = {"kernel": "k_engine_step", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("ensemble"),
+    roofline = {"kernel": "k_engine_run", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("k_engine_run", "ensemble"),
                 "bytes_per_entry": bpe, "entries_per_launch": round(entries / launches_per_step, 1),
                 "launch_us": round(per_launch_s * 1e6, 3), "sampled_launches": kn,
                 "peak_source": f"{peak_kind} hbm_gbs"}
