@@ -44,6 +44,8 @@ def lib():
                               _i32p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_double,
                               C.c_uint64, C.c_int64]
         L.orc_run.restype = C.c_int
+        L.orc_run_rule.argtypes = L.orc_run.argtypes + [C.c_int32]
+        L.orc_run_rule.restype = C.c_int
         L.orc_issa_run.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _i32p, C.c_double,
                                    C.c_uint64]
@@ -136,21 +138,28 @@ class OracleError(RuntimeError):
     pass
 
 
+# Transfer rules (Sec. II.C): the count the diffusion draw of a period uses.
+RULE_MEAN = 0   # N-bar, the mean occupancy (Eq. 3): the method
+RULE_END = 1    # N(tau_k): first-order splitting (Sec. III.B, Fig. 7)
+RULE_MID = 2    # N(tau_k / 2): the half-step ("median") reading
+
+
 def run(mesh, model, counts, t_end: float, seed: int, t0: float = 0.0, period0: int = 0,
-        max_periods: int = -1):
+        max_periods: int = -1, rule: int = RULE_MEAN):
     """Algorithm 1 from ``t0`` towards ``t_end`` (at most ``max_periods``
-    periods).  Returns (counts [T][S] int32, t, period)."""
+    periods) with the given transfer rule.  Returns (counts [T][S] int32, t,
+    period)."""
     S, R, D, lhs, rhs, k, mask = _model_arrays(model)
     c = np.ascontiguousarray(counts, np.int32).copy()
     assert c.shape == (mesh.n_tets, S)
     t = C.c_double(t0)
     p = C.c_int64(period0)
-    rc = lib().orc_run(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
-                       lhs.ctypes.data, rhs.ctypes.data, k.ctypes.data, _ptr(mask),
-                       float(model.tau_scale), c, C.byref(t), C.byref(p), float(t_end),
-                       int(seed), int(max_periods))
+    rc = lib().orc_run_rule(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
+                            lhs.ctypes.data, rhs.ctypes.data, k.ctypes.data, _ptr(mask),
+                            float(model.tau_scale), c, C.byref(t), C.byref(p), float(t_end),
+                            int(seed), int(max_periods), int(rule))
     if rc != 0:
-        raise OracleError(f"orc_run failed with code {rc}")
+        raise OracleError(f"orc_run_rule failed with code {rc}")
     return c, t.value, p.value
 
 

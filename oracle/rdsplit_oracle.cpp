@@ -265,7 +265,19 @@ struct Problem {
     const double* k;
     const uint8_t* mask;     // [R][T] or null
     double tau_scale;
+    int rule;                // transfer rule: kRuleMean, kRuleEnd or kRuleMid
 };
+
+// Which count of a period the diffusion draw of Step 3.2 uses (Sec. II.C).
+//  kRuleMean  N-bar, the mean occupancy over the period (Eq. 3): the method.
+//  kRuleEnd   N(tau_k), the count after the reaction phase: first-order
+//             splitting, the comparison method of Sec. III.B (Fig. 7).
+//  kRuleMid   N(tau_k / 2), the count at the middle of the period: the
+//             "median" reading of N that half-step (Strang) splitting
+//             amounts to (Sec. II.C, Fig. 4).
+const int kRuleMean = 0;
+const int kRuleEnd = 1;
+const int kRuleMid = 2;
 
 // Setup (Sec. II.A; Algorithm 1, precompute):
 //   g[t][f] = A_tf / (V_t * dist_tf) for faces with a neighbour, else 0;
@@ -325,9 +337,14 @@ double avogadro_volume(double vol_m3) { return kAvogadro * (vol_m3 * 1000.0); }
 // tet's current counts; an event whose time would reach tau_k is discarded.
 // On every event, before the counts change, the occupancy integral of each
 // species whose count changes is advanced: occ += N * (t_event - t_last).
+// Nmid receives the counts at tau_k / 2: those after every event whose time
+// is below tau_k / 2.
 void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t seed,
-               int64_t* N, double* occ, double* tlast, bool* touched) {
+               int64_t* N, double* occ, double* tlast, bool* touched, int64_t* Nmid) {
+    for (int s = 0; s < P.S; ++s) Nmid[s] = N[s];
     if (P.R == 0) return;
+    const double half = 0.5 * tau_k;
+    bool past_half = false;
     double c[kMaxReactions];
     double avv = avogadro_volume(P.vol[t]);
     for (int r = 0; r < P.R; ++r) {
@@ -359,6 +376,10 @@ void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t 
         double u1 = st.u01_open0();
         double tn = tc + (-own_log(u1)) / a0;
         if (tn >= tau_k) break;
+        if (!past_half && tn >= half) {
+            for (int s = 0; s < P.S; ++s) Nmid[s] = N[s];
+            past_half = true;
+        }
         double target = st.u01() * a0;
         int mu = -1;
         double cum = 0.0;
@@ -380,6 +401,8 @@ void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t 
         }
         tc = tn;
     }
+    if (!past_half)
+        for (int s = 0; s < P.S; ++s) Nmid[s] = N[s];
     for (int s = 0; s < P.S; ++s)
         if (touched[s]) occ[s] = occ[s] + (double)N[s] * (tau_k - tlast[s]);
 }
@@ -388,7 +411,9 @@ void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t 
 // (Algorithm 1, Step 3; Eq. 2 and Eq. 3; Sec. II.B).
 //  3.1  N-bar = occupancy / tau_k for a species whose count changed during
 //       the period; otherwise N-bar = N exactly.  A fractional N-bar is made an
-//       integer N* by unbiased stochastic rounding.
+//       integer N* by unbiased stochastic rounding.  Under the comparison
+//       rules N* is instead N(tau_k) (kRuleEnd) or N(tau_k / 2) (kRuleMid),
+//       both integers, and no rounding draw is made.
 //  3.2  n = Binomial(N*, zeta), capped at the molecules present, N(tau_k).
 //  3.3  n is split over the faces multinomially by conditional binomials in
 //       canonical face order, p_i = w_i / (w_i + ... + w_3), the last face
@@ -402,13 +427,15 @@ void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t 
 //  faster on the GPU than the double-precision samplers.
 void diffuse_tet_species(const Problem& P, const Geometry& geo, int t, int s, uint32_t period,
                          double tau_k, uint64_t seed, int64_t Nt, bool touched, double occ,
-                         int64_t out[4]) {
+                         int64_t Nmid, int64_t out[4]) {
     out[0] = out[1] = out[2] = out[3] = 0;
     double Gt = geo.G[t];
     double zeta = zeta_of(tau_k, P.D[s], Gt);
     if (!(zeta > 0.0) || Nt <= 0) return;
     int64_t Nstar = Nt;
-    if (touched) {
+    if (P.rule == kRuleMid) {
+        Nstar = Nmid;
+    } else if (P.rule == kRuleMean && touched) {
         Stream rs(seed, (uint32_t)t, period, kRounding, (uint32_t)s);
         double nbar = occ / tau_k;
         double fl = std::floor(nbar);
@@ -493,7 +520,7 @@ void orc_binomial_many(uint64_t seed, uint32_t period, int64_t n, double p, int6
 // species diffuses.
 double orc_tau(int32_t T, const int32_t* adj, const double* vol, const double* area,
                const double* dist, int32_t S, const double* D, double tau_scale) {
-    Problem P{T, S, 0, adj, vol, area, dist, D, nullptr, nullptr, nullptr, nullptr, tau_scale};
+    Problem P{T, S, 0, adj, vol, area, dist, D, nullptr, nullptr, nullptr, nullptr, tau_scale, kRuleMean};
     return setup_geometry(P).tau;
 }
 
@@ -502,13 +529,16 @@ double orc_tau(int32_t T, const int32_t* adj, const double* vol, const double* a
 // the global period index used in the random-number keys.  Returns 0, or a
 // negative code: -1 bad arguments, -2 conservation or sign violated,
 // -3 int32 overflow.
-int orc_run(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
-            int32_t S, const double* D, int32_t R, const int32_t* lhs, const int32_t* rhs,
-            const double* k, const uint8_t* mask, double tau_scale,
-            int32_t* counts, double* t_io, int64_t* period_io, double t_end, uint64_t seed,
-            int64_t max_periods) {
+// `rule` selects the count the diffusion draw uses (kRuleMean, the method;
+// kRuleEnd or kRuleMid, the comparison rules of Sec. II.C and III.B).
+int orc_run_rule(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
+                 int32_t S, const double* D, int32_t R, const int32_t* lhs, const int32_t* rhs,
+                 const double* k, const uint8_t* mask, double tau_scale,
+                 int32_t* counts, double* t_io, int64_t* period_io, double t_end, uint64_t seed,
+                 int64_t max_periods, int32_t rule) {
     if (T <= 0 || S <= 0 || S > kMaxSpecies || R < 0 || R > kMaxReactions) return -1;
-    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale};
+    if (rule != kRuleMean && rule != kRuleEnd && rule != kRuleMid) return -1;
+    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale, rule};
     Geometry geo = setup_geometry(P);
     std::vector<int64_t> N((size_t)T * S), rem((size_t)T * S), out((size_t)T * S * 4);
     for (size_t i = 0; i < N.size(); ++i) N[i] = counts[i];
@@ -533,19 +563,19 @@ int orc_run(int32_t T, const int32_t* adj, const double* vol, const double* area
         // Step 2 and 3, tet by tet; every draw is keyed by (period, tet), so
         // the order of this loop does not matter.
         for (int t = 0; t < T; ++t) {
-            int64_t Nt[kMaxSpecies];
+            int64_t Nt[kMaxSpecies], Nmid[kMaxSpecies];
             double occ[kMaxSpecies], tl[kMaxSpecies];
             bool touched[kMaxSpecies];
             for (int s = 0; s < S; ++s) {
                 Nt[s] = N[(size_t)t * S + s];
                 occ[s] = 0.0; tl[s] = 0.0; touched[s] = false;
             }
-            react_tet(P, t, (uint32_t)period, tau_k, seed, Nt, occ, tl, touched);
+            react_tet(P, t, (uint32_t)period, tau_k, seed, Nt, occ, tl, touched, Nmid);
             for (int s = 0; s < S; ++s) {
                 if (Nt[s] < 0) return -2;
                 int64_t o[4];
                 diffuse_tet_species(P, geo, t, s, (uint32_t)period, tau_k, seed, Nt[s], touched[s],
-                                    occ[s], o);
+                                    occ[s], Nmid[s], o);
                 int64_t sum = 0;
                 for (int f = 0; f < 4; ++f) { out[((size_t)t * S + s) * 4 + f] = o[f]; sum += o[f]; }
                 rem[(size_t)t * S + s] = Nt[s] - sum;
@@ -582,6 +612,16 @@ int orc_run(int32_t T, const int32_t* adj, const double* vol, const double* area
     return 0;
 }
 
+// Algorithm 1 with the method's own transfer rule (N-bar, Eq. 3).
+int orc_run(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
+            int32_t S, const double* D, int32_t R, const int32_t* lhs, const int32_t* rhs,
+            const double* k, const uint8_t* mask, double tau_scale,
+            int32_t* counts, double* t_io, int64_t* period_io, double t_end, uint64_t seed,
+            int64_t max_periods) {
+    return orc_run_rule(T, adj, vol, area, dist, S, D, R, lhs, rhs, k, mask, tau_scale, counts, t_io, period_io,
+                        t_end, seed, max_periods, kRuleMean);
+}
+
 // Steps 2 and 3 of one period (reactions, then the diffusion draws) for the
 // tets t_begin .. t_end-1 only, from counts [T][S] (only those tets' rows are
 // read).  Writes their out-slots out[(t - t_begin)][S][4] and the molecules
@@ -595,21 +635,21 @@ int orc_period_tets(int32_t T, const int32_t* adj, const double* vol, const doub
                     int32_t* out, int32_t* rem) {
     if (T <= 0 || S <= 0 || S > kMaxSpecies || R < 0 || R > kMaxReactions) return -1;
     if (t_begin < 0 || t_end > T || t_begin > t_end) return -1;
-    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale};
+    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale, kRuleMean};
     Geometry geo = setup_geometry(P);
     for (int t = t_begin; t < t_end; ++t) {
-        int64_t Nt[kMaxSpecies];
+        int64_t Nt[kMaxSpecies], Nmid[kMaxSpecies];
         double occ[kMaxSpecies], tl[kMaxSpecies];
         bool touched[kMaxSpecies];
         for (int s = 0; s < S; ++s) {
             Nt[s] = counts[(size_t)t * S + s];
             occ[s] = 0.0; tl[s] = 0.0; touched[s] = false;
         }
-        react_tet(P, t, (uint32_t)period, tau_k, seed, Nt, occ, tl, touched);
+        react_tet(P, t, (uint32_t)period, tau_k, seed, Nt, occ, tl, touched, Nmid);
         for (int s = 0; s < S; ++s) {
             if (Nt[s] < 0) return -2;
             int64_t o[4];
-            diffuse_tet_species(P, geo, t, s, (uint32_t)period, tau_k, seed, Nt[s], touched[s], occ[s], o);
+            diffuse_tet_species(P, geo, t, s, (uint32_t)period, tau_k, seed, Nt[s], touched[s], occ[s], Nmid[s], o);
             int64_t sum = 0;
             for (int f = 0; f < 4; ++f) { out[((size_t)(t - t_begin) * S + s) * 4 + f] = (int32_t)o[f]; sum += o[f]; }
             rem[(size_t)(t - t_begin) * S + s] = (int32_t)(Nt[s] - sum);

@@ -4,6 +4,8 @@ Nothing here calls the oracle or the CUDA path.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 from scipy.linalg import expm
 
@@ -95,3 +97,16 @@ def one_tet_mesh(vol=1e-19):
     from paper_1512_03126_gb300.inputs import Mesh
     return Mesh(adj=np.full((1, 4), -1, np.int32), vol=np.array([vol]), area=np.full((1, 4), 1e-13),
                 dist=np.zeros((1, 4)), centroid=np.zeros((1, 3)), shape=(), size=(1, 1, 1))
+
+
+def binomial_of_shifted_poisson(n0: int, lam: float, p: float, kmax: int) -> np.ndarray:
+    """pmf over k = 0..kmax of Binomial(n0 + M, p) with M ~ Poisson(lam)."""
+    out = np.zeros(kmax + 1)
+    mmax = int(lam + 12 * math.sqrt(lam) + 30)
+    for m in range(mmax + 1):
+        wm = math.exp(-lam + m * math.log(lam) - math.lgamma(m + 1)) if lam > 0 else float(m == 0)
+        n = n0 + m
+        for k in range(min(n, kmax) + 1):
+            out[k] += wm * math.exp(math.lgamma(n + 1) - math.lgamma(k + 1) - math.lgamma(n - k + 1)
+                                    + k * math.log(p) + (n - k) * math.log1p(-p))
+    return out

@@ -9,8 +9,8 @@ import pytest
 from scipy.stats import binom
 
 from paper_1512_03126_gb300 import inputs as I
-from tests.laws import (birth_death_ABC, chi2_pvalue, one_period_matrix, one_tet_mesh,
-                        two_tet_mesh)
+from tests.laws import (binomial_of_shifted_poisson, birth_death_ABC, chi2_pvalue, one_period_matrix,
+                        one_tet_mesh, two_tet_mesh)
 
 
 def _src(counts):
@@ -152,6 +152,61 @@ def test_mean_corrected_transfer(oracle):
     se = n.std() / math.sqrt(n.size)
     assert abs(n.mean() - expect) < 4 * se
     assert abs(n.mean() - zeta * (5 + a_tau)) > 20 * se
+
+
+def _influx_two_tets(a_tau: float, zeta: float):
+    """Two tets; tet 0 holds 5 molecules and has a zero-order influx of
+    a_tau molecules per period (mean); tau set so that zeta = tau * d."""
+    vol = 1e-19
+    mesh = two_tet_mesh((vol, vol))
+    D = 1e-12
+    model0 = I.diffusion_model(D)
+    model0.tau_scale = zeta
+    tau = oracle_tau(mesh, model0)
+    k_in = a_tau / (tau * 6.02214076e23 * vol * 1e3)
+    mask = np.array([[1, 0]], np.uint8)
+    model = I.Model(D=np.array([D]), lhs=np.zeros((1, 1), np.int32), rhs=np.ones((1, 1), np.int32),
+                    k=np.array([k_in]), mask=mask, tau_scale=zeta)
+    return mesh, model, np.array([[5], [0]], np.int32)
+
+
+def oracle_tau(mesh, model):
+    from oracle import oracle as O
+    return O.tau(mesh, model)
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+def test_comparison_rules_exact_laws(oracle, rule):
+    """The comparison transfer rules of Sec. II.C and III.B.  With a Poisson
+    influx (a tau per period) into a tet holding N0 = 5 and no other
+    reaction, the count at time s of the period is N0 + Poisson(a s), so the
+    number sent to the other tet in one period is exactly
+    Binomial(N0 + Poisson(a tau), zeta) under first-order splitting (N at
+    tau) and Binomial(N0 + Poisson(a tau / 2), zeta) under the half-step
+    reading (N at tau / 2).  The method's rule (N-bar) has the second one's
+    mean but not its law (the random part of N-bar has variance a tau / 3,
+    that of N(tau / 2) a tau / 2), and the test checks that the law tells
+    them apart."""
+    zeta, a_tau = 0.5, 20.0
+    mesh, model, c0 = _influx_two_tets(a_tau, zeta)
+    n = np.array([oracle.run(mesh, model, c0, np.inf, s, max_periods=1, rule=rule)[0][1, 0]
+                  for s in range(20000)])
+    lam = a_tau if rule == 1 else a_tau / 2
+    law = binomial_of_shifted_poisson(5, lam, zeta, int(n.max()) + 20)
+    assert chi2_pvalue(np.bincount(n, minlength=law.size), law) > 1e-4
+    if rule == 2:
+        mean_rule = np.array([oracle.run(mesh, model, c0, np.inf, s, max_periods=1)[0][1, 0]
+                              for s in range(20000)])
+        assert chi2_pvalue(np.bincount(mean_rule, minlength=law.size), law) < 1e-6
+
+
+def test_rules_agree_without_reactions(oracle):
+    """Without reactions N-bar = N(tau/2) = N(tau): the three rules give the
+    same counts, draw for draw."""
+    w = I.diffusion_cube(4, 1e-6, 0.2, 11, 600, 0.004, 3)
+    base = oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed)[0]
+    for rule in (1, 2):
+        assert np.array_equal(oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed, rule=rule)[0], base)
 
 
 def test_point_source_spreads_at_6Dt(oracle):

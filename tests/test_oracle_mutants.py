@@ -27,9 +27,21 @@ MUTANTS = {
         "    double z = tau_k * (D * Gt);\n    return 1.0 - own_exp(-(z > 1.0 ? 1.0 : z));",
         [lambda o: L.test_exact_law_of_pure_diffusion(o, 300)]),
     "no_mean_correction": (
-        "    if (touched) {\n        Stream rs(",
-        "    if (false) {\n        Stream rs(",
+        "    } else if (P.rule == kRuleMean && touched) {\n        Stream rs(",
+        "    } else if (false) {\n        Stream rs(",
         [L.test_mean_corrected_transfer]),
+    "mid_rule_takes_end_count": (
+        "        Nstar = Nmid;",
+        "        Nstar = Nt;",
+        [lambda o: L.test_comparison_rules_exact_laws(o, 2)]),
+    "mid_snapshot_at_end": (
+        "if (!past_half && tn >= half) {",
+        "if (!past_half && tn >= tau_k) {",
+        [lambda o: L.test_comparison_rules_exact_laws(o, 2)]),
+    "end_rule_rounds_occupancy": (
+        "    } else if (P.rule == kRuleMean && touched) {\n        Stream rs(",
+        "    } else if (touched) {\n        Stream rs(",
+        [lambda o: L.test_comparison_rules_exact_laws(o, 1)]),
     "split_without_renormalisation": (
         "int64_t nf = binomial(m, g[f] / suf[f], st);",
         "int64_t nf = binomial(m, g[f] / geo.G[t], st);",
