@@ -95,6 +95,24 @@ int rdsplit_set_model(rdsplit_mesh_t mesh, int32_t n_species, const double* D,
                       int32_t n_reactions, const int32_t* lhs, const int32_t* rhs,
                       const double* k, const uint8_t* rxn_tet_mask, double tau_scale);
 
+/*
+ * Transfer rule: which count of a period the diffusion draw of Step 3.2 uses
+ * (Sec. II.C; the comparison of Sec. III.B, Fig. 7).
+ *   RDSPLIT_TRANSFER_MEAN  N-bar, the mean occupancy over the period (Eq. 3);
+ *                          the method, and the default
+ *   RDSPLIT_TRANSFER_END   N(tau_k), the count after the reaction phase:
+ *                          first-order operator splitting
+ *   RDSPLIT_TRANSFER_MID   N(tau_k / 2), the count at mid-period: the reading
+ *                          of N that half-step (Strang) splitting amounts to
+ * Without reactions the three give identical results.  The rule is kept
+ * across rdsplit_set_model and travels with the handle into the batched
+ * engine.  Returns RDSPLIT_EINVAL for another value.
+ */
+#define RDSPLIT_TRANSFER_MEAN 0
+#define RDSPLIT_TRANSFER_END 1
+#define RDSPLIT_TRANSFER_MID 2
+int rdsplit_set_transfer_rule(rdsplit_mesh_t mesh, int32_t rule);
+
 /* Set counts from host memory, int32 [n_tets][n_species], all >= 0. */
 int rdsplit_set_counts(rdsplit_mesh_t mesh, const int32_t* counts);
 /* Same from device memory (same layout), e.g. a torch CUDA tensor. */

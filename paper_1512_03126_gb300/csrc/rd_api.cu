@@ -243,6 +243,15 @@ int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol, c
     return cleanup(RDSPLIT_OK);
 }
 
+int rdsplit_set_transfer_rule(rdsplit_mesh_t h, int32_t rule) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_transfer_rule: NULL handle");
+    if (rule != RDSPLIT_TRANSFER_MEAN && rule != RDSPLIT_TRANSFER_END && rule != RDSPLIT_TRANSFER_MID)
+        return fail(RDSPLIT_EINVAL, "rdsplit_set_transfer_rule: rule must be 0, 1 or 2");
+    h->rule = rule;
+    h->mp.rule = rule;
+    return RDSPLIT_OK;
+}
+
 int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, const int32_t* lhs,
                       const int32_t* rhs, const double* k, const uint8_t* mask, double tau_scale) {
     if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_model: NULL handle");
@@ -280,6 +289,7 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
     }
     mp.any_reaction = R > 0 ? 1 : 0;
     mp.has_mask = mask ? 1 : 0;
+    mp.rule = h->rule;
     finish_model_params(mp);
 
     h->free_model();

@@ -40,6 +40,7 @@ struct rdsplit_mesh {
     int2* N2 = nullptr;        // one species: {count, count} of two period parities (batched engine)
     rdk::ModelParams mp{};
     bool has_model = false;
+    int32_t rule = 0;          // transfer rule, kept across rdsplit_set_model
     // sampled kernel timing
     int32_t timing_stride = 0;
     std::vector<cudaEvent_t> ev_pool;

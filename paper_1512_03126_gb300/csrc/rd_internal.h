@@ -36,7 +36,15 @@ struct ModelParams {
     int8_t rs1[kMaxR], rs2[kMaxR];
     float kf[kMaxR];
     uint32_t kpos;
+    // Transfer rule of the diffusion draw (Sec. II.C): kRuleMean (N-bar,
+    // Eq. 3, the method), kRuleEnd (N at tau_k, first-order splitting) or
+    // kRuleMid (N at tau_k / 2).
+    int32_t rule;
 };
+
+constexpr int32_t kRuleMean = 0;
+constexpr int32_t kRuleEnd = 1;
+constexpr int32_t kRuleMid = 2;
 
 // Fill the pre-test fields of a ModelParams whose lhs/k/order are set.
 void finish_model_params(ModelParams& mp);

@@ -37,14 +37,20 @@ __device__ __forceinline__ int64_t incoming(const int32_t* __restrict__ op, int4
 // Reaction phase of one tet (Algorithm 1, Step 2 and 2.1): Gillespie's
 // direct method over [0, tau_k); the first event at or past tau_k is
 // discarded.  Before a species' count changes, its occupancy integral
-// advances by N * (t_event - t_last).  The tet's volume, reaction mask and
+// advances by N * (t_event - t_last).  Under the half-step rule
+// (kRuleMid), Nmid receives the counts at tau_k / 2: those after every event
+// whose time is below tau_k / 2.  The tet's volume, reaction mask and
 // single-precision (N_A V, 1/(N_A V)) come in by value: a non-inlined
 // function that took the mesh by reference would pin the caller's copy of
 // it in local memory.
 static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint32_t period, double tau_k,
                                               uint64_t seed, double vol_t, uint32_t on, float2 avf, int64_t* N,
-                                              double* occ, double* tl, uint32_t& touched, uint32_t* err) {
+                                              double* occ, double* tl, uint32_t& touched, int64_t* Nmid,
+                                              uint32_t* err) {
     const double avv = kAvogadro * (vol_t * 1000.0);
+    const bool want_mid = mp.rule == kRuleMid;
+    const double half = 0.5 * tau_k;
+    bool past_half = false;
     // Per-reaction constants of this tet, computed once: the same values as
     // recomputing them at every event (c = k N_A V, k, or k / (N_A V)).
     double c[kMaxR];
@@ -105,6 +111,10 @@ static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint
         const double u1 = ((double)x53 + 1.0) * (1.0 / 9007199254740992.0);
         double tn = tc + (-rdd::own_log(u1)) / a0;
         if (tn >= tau_k) break;
+        if (want_mid && !past_half && tn >= half) {
+            for (int s = 0; s < mp.S; ++s) Nmid[s] = N[s];
+            past_half = true;
+        }
         double target = st.u01() * a0;
         int mu = -1;
         double cum = 0.0;
@@ -127,6 +137,8 @@ static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint
         tc = tn;
         if (++events >= kEventCap) { atomicOr(err, kErrEventCap); break; }
     }
+    if (want_mid && !past_half)
+        for (int s = 0; s < mp.S; ++s) Nmid[s] = N[s];
     for (int s = 0; s < mp.S; ++s)
         if ((touched >> s) & 1u) occ[s] = occ[s] + (double)N[s] * (tau_k - tl[s]);
 }
@@ -135,16 +147,21 @@ static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint
 // Sec. II.B): N* from the occupancy (stochastic rounding of N-bar when the
 // count changed during the period, else N), n = min(Binomial(N*, zeta), N),
 // split over the faces by conditional binomials; below N* = kMoleculeCut the
-// same law one molecule at a time against the cumulative thresholds.
+// same law one molecule at a time against the cumulative thresholds.  Under
+// the half-step comparison rule N* is N(tau_k / 2) (Nmid); under the
+// first-order rule the caller passes touched = false, so N* = N(tau_k).
 static __device__ __noinline__ int4 diffuse(const double* __restrict__ G, const double* __restrict__ gface, int t,
                                             int s, double Dsp, uint32_t period, double tau_k, uint64_t seed,
-                                            int64_t Nt, bool touched, double occ, uint4 C) {
+                                            int64_t Nt, bool touched, double occ, int64_t Nmid, int32_t rule,
+                                            uint4 C) {
     int4 o = make_int4(0, 0, 0, 0);
     double Gt = G[t];
     double z = zeta_of(tau_k, Dsp, Gt);
     if (!(z > 0.0) || Nt <= 0) return o;
     int64_t Nstar = Nt;
-    if (touched) {
+    if (touched && rule == kRuleMid) {
+        Nstar = Nmid;                          // N(tau_k / 2), an integer: no rounding draw
+    } else if (touched) {
         rdd::Stream rs(seed, (uint32_t)t, period, rdd::kPurposeRounding, (uint32_t)s);
         double nbar = occ / tau_k;
         double fl = floor(nbar);
@@ -279,6 +296,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
     uint32_t bad = 0;
     uint32_t touched = 0;
     double occ[SA];
+    int64_t nmid[SA];
     if (kReact) {
         uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
         bool possible = false;
@@ -300,7 +318,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
                 tl[sp] = 0.0;
             }
             react_tet(mp, t, period, tau_k, seed, m.vol[t], mp.has_mask ? m.mask[t] : 0xffffffffu, m.avv[t], N64, occ,
-                      tl, touched, err);
+                      tl, touched, nmid, err);
 #pragma unroll
             for (int sp = 0; sp < SA; ++sp) {
                 if (sp >= S) break;
@@ -316,7 +334,8 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
         if (sp >= S) break;
         int32_t Nt = N[sp];
         int4 x = make_int4(0, 0, 0, 0);
-        bool tch = kReact && ((touched >> sp) & 1u);
+        // first-order splitting draws from N(tau_k): the untouched path
+        bool tch = kReact && ((touched >> sp) & 1u) && mp.rule != kRuleEnd;
         if (Nt > 0) {
             if (!tch && Nt < kWarpSplitMin) {
                 x = split_molecules(seed, period, t, sp, Nt, (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
@@ -326,6 +345,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
                 continue;
             } else {
                 x = diffuse(m.G, m.g, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
+                            tch ? nmid[sp] : (int64_t)Nt, mp.rule,
                             (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
             }
         }

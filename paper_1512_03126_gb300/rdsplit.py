@@ -63,6 +63,7 @@ def _declare(L):
         "rdsplit_engine_destroy": ([vp], C.c_int),
         "rdsplit_ensemble_run": ([i32, vp, vp, vp], C.c_int),
         "rdsplit_engine_set_timing": ([vp, i32], C.c_int),
+        "rdsplit_set_transfer_rule": ([vp, i32], C.c_int),
         "rdsplit_engine_set_concurrency": ([vp, i32, i32], C.c_int),
         "rdsplit_engine_set_bitmap_smem": ([vp, i32], C.c_int),
         "rdsplit_engine_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)], C.c_int),
@@ -252,6 +253,15 @@ def rdsplit_engine_destroy(e):
     _check(lib().rdsplit_engine_destroy(e))
 
 
+RDSPLIT_TRANSFER_MEAN = 0   # N-bar, the mean occupancy (Eq. 3): the method
+RDSPLIT_TRANSFER_END = 1    # N(tau_k): first-order splitting
+RDSPLIT_TRANSFER_MID = 2    # N(tau_k / 2): the half-step reading
+
+
+def rdsplit_set_transfer_rule(h, rule: int):
+    _check(lib().rdsplit_set_transfer_rule(h, int(rule)))
+
+
 def rdsplit_engine_set_concurrency(e, in_flight: int, cluster: int = 4):
     _check(lib().rdsplit_engine_set_concurrency(e, int(in_flight), int(cluster)))
 
@@ -347,11 +357,13 @@ class Simulation:
     """One mesh + model handle: ``Simulation(mesh, model)``, then
     ``set_counts``, ``run``, ``counts``."""
 
-    def __init__(self, mesh, model, counts=None, stream=None):
+    def __init__(self, mesh, model, counts=None, stream=None, rule: int = RDSPLIT_TRANSFER_MEAN):
         self.h = rdsplit_mesh_create(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist)
         try:
             rdsplit_set_model(self.h, model.n_species, model.D, model.n_reactions, model.lhs, model.rhs,
                               model.k, model.mask, model.tau_scale)
+            if rule != RDSPLIT_TRANSFER_MEAN:
+                rdsplit_set_transfer_rule(self.h, rule)
             if stream is not None:
                 rdsplit_set_stream(self.h, stream)
             if counts is not None:

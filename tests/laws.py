@@ -110,3 +110,54 @@ def binomial_of_shifted_poisson(n0: int, lam: float, p: float, kmax: int) -> np.
             out[k] += wm * math.exp(math.lgamma(n + 1) - math.lgamma(k + 1) - math.lgamma(n - k + 1)
                                     + k * math.log(p) + (n - k) * math.log1p(-p))
     return out
+
+
+def hop_generator(mesh, D: float) -> np.ndarray:
+    """K with dm/dt = K m for the mean counts of pure diffusion in continuous
+    time (the reaction-diffusion master equation's mean; K[u, t] = rate of a
+    molecule's hop t -> u, K[t, t] = -(its total hop rate))."""
+    T = mesh.n_tets
+    rate = face_rates(mesh, D)
+    K = np.zeros((T, T))
+    for t in range(T):
+        for f in range(4):
+            u = mesh.adj[t, f]
+            if u >= 0:
+                K[u, t] += rate[t, f]
+        K[t, t] -= rate[t].sum()
+    return K
+
+
+def influx_ode_mean(mesh, D: float, a: np.ndarray, t: float) -> np.ndarray:
+    """Exact mean counts at time t from empty, under a constant influx a
+    [molecules/s per tet] and diffusion: m(t) = int_0^t exp(K s) a ds (the
+    master equation of a linear system has these means exactly)."""
+    T = mesh.n_tets
+    aug = np.zeros((T + 1, T + 1))
+    aug[:T, :T] = hop_generator(mesh, D)
+    aug[:T, T] = a
+    return expm(aug * t)[:T, T]
+
+
+def influx_split_mean(mesh, D: float, a: np.ndarray, tau: float, periods: int, c: float) -> np.ndarray:
+    """Exact mean counts after `periods` operator-split periods from empty,
+    under a constant influx a and pure diffusion, when the diffusion draw of
+    a period uses a count whose mean is m + c a tau (m the count at the start
+    of the period): c = 1/2 for the mean occupancy and for the count at
+    mid-period, c = 1 for the count at the end (Sec. II.C).  Each molecule
+    counted leaves t through face f with probability tau * rate_tf."""
+    rate = face_rates(mesh, D)
+    T = mesh.n_tets
+    zeta = tau * rate.sum(1)
+    W = np.zeros((T, T))
+    for t in range(T):
+        d = rate[t].sum()
+        for f in range(4):
+            u = mesh.adj[t, f]
+            if u >= 0 and d > 0:
+                W[u, t] += rate[t, f] / d
+    m = np.zeros(T)
+    for _ in range(periods):
+        out = zeta * (m + c * a * tau)
+        m = m + a * tau - out + W @ out
+    return m
