@@ -60,6 +60,12 @@ __device__ __forceinline__ bool zero_order_on(const SlotDesc& d, const ModelPara
     return (on & d.zero_order) != 0u;
 }
 
+// Fire-and-forget integer add to global memory (no value comes back, so the
+// warp does not wait for the L2 round trip).
+__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
 // Position of the k-th (0-based) set bit of w; w has more than k set bits.
 __device__ __forceinline__ int select_bit(uint32_t w, uint32_t k) {
     int pos = 0;
@@ -135,6 +141,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
     __shared__ int32_t item_s;
     __shared__ uint32_t total_s[2];   // molecules of a reaction-free simulation; [1] != 0: above 2^31-1
     __shared__ uint32_t wbuf[kWarps][kGroup * 32];
+    __shared__ int32_t slowq[kWarps * 64];   // per warp: tets deferred to the rounds with calls
     extern __shared__ uint32_t sbits[];   // [2][rows * kRowStride]: this CTA's runs of both bitmaps
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
@@ -146,6 +153,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
     };
     const int lane = threadIdx.x & 31;
     const int gw = rank * kWarps + (threadIdx.x >> 5);
+    const unsigned lane_lt = (1u << lane) - 1u;
     uint32_t* wb = wbuf[threadIdx.x >> 5];
     unsigned long long done = 0;
     for (;;) {
@@ -238,6 +246,77 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             // shared memory) or the global bitmap
             uint32_t* bcur = in_smem ? sbits + r * rw + (threadIdx.x >> 5) * 8 : d.bits[r];
             const bool more = q + 1 < d.q1;
+            // Transfer of one tet's molecules (kept and leaving) into the next
+            // counts, and its bits in the next bitmap.
+            auto scatter = [&](int t, const int4& sr, const int32_t* N, const int4* o) {
+                const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
+                bool keep = kReact && zero_order_on(d, mp, t);
+                bool send[4] = {false, false, false, false};
+#pragma unroll
+                for (int s = 0; s < SA; ++s) {
+                    if (s >= S) break;
+                    int32_t* Ns = Nnext + (int64_t)s * T * cstride;
+                    if (N[s] > 0) {
+                        if (exact) {
+                            const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
+                            if (old > 2147483647 - N[s]) bad |= kErrOverflow;
+                        } else {
+                            red_add(Ns + (int64_t)t * cstride, N[s]);
+                        }
+                        keep = true;
+                    }
+                    const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        if (ov[f] <= 0) continue;
+                        if (nbr[f] < 0) { bad |= kErrNegative; continue; }
+                        int32_t* dst = Ns + (int64_t)(nbr[f] >> 2) * cstride;
+                        if (exact) {
+                            const int32_t old = atomicAdd(dst, ov[f]);
+                            if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
+                        } else {
+                            red_add(dst, ov[f]);
+                        }
+                        send[f] = true;
+                    }
+                }
+                if (more) {
+                    if (keep) atomicOr(word_ptr(r ^ 1, t >> 5), 1u << (t & 31));
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        if (!send[f]) continue;
+                        const int u = nbr[f] >> 2;
+                        atomicOr(word_ptr(r ^ 1, u >> 5), 1u << (u & 31));
+                    }
+                }
+            };
+            // One round over the first n (<= 32) deferred tets of this warp's
+            // queue, with the full per-tet step (reactions and the
+            // non-inlined samplers).  The whole warp calls it.
+            auto slow_round = [&](int n) {
+                const bool live = lane < n;
+                const int t = live ? slowq[(threadIdx.x >> 5) * 64 + lane] : 0;
+                uint32_t heavy = 0;
+                int32_t N[SA];
+                int4 o[SA];
+                int4 sr = make_int4(-1, -1, -1, -1);
+                uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+                if (live) {
+                    sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
+                    if (use_packed) pre = d.packed[2 * t + 1];
+#pragma unroll
+                    for (int s = 0; s < SA; ++s) {
+                        if (s >= S) break;
+                        int32_t* p = Ncur + ((int64_t)s * T + t) * cstride;
+                        N[s] = *p;
+                        *p = 0;
+                    }
+                    bad |= step_tet<SA, kReact, true>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o, &heavy,
+                                                      err, tstride, use_packed, pre);
+                }
+                warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride, use_packed, pre);
+                if (live) scatter(t, sr, N, o);
+            };
             for (int g0 = 0; g0 < W; g0 += kGroup * 32 * kW) {
                 uint32_t wds[kGroup];
 #pragma unroll
@@ -265,6 +344,12 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                 const uint32_t n_act = __shfl_sync(kAll, inc, 31);
                 const uint32_t before = inc - c;
                 done += n_act;
+                // Entries whose tet needs a non-inlined sampler (a count of
+                // kMoleculeCut or more, or a reaction event) wait in the warp's
+                // queue and run in rounds of their own, so that the common
+                // round holds no call (a call there makes the compiler spill
+                // the round's live registers to local memory).
+                int n_slow = 0;                       // warp-uniform
                 for (uint32_t j0 = 0; j0 < n_act; j0 += 32) {
                     const uint32_t j = j0 + (uint32_t)lane;
                     const bool live = j < n_act;
@@ -297,6 +382,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                     int4 o[SA];
                     int4 sr = make_int4(-1, -1, -1, -1);
                     uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+                    bool light = false;
                     if (live) {
                         // the tet's record and counts, loaded together
                         sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
@@ -304,55 +390,39 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
 #pragma unroll
                         for (int s = 0; s < SA; ++s) {
                             if (s >= S) break;
-                            int32_t* p = Ncur + ((int64_t)s * T + t) * cstride;
-                            N[s] = *p;
-                            *p = 0;
+                            N[s] = Ncur[((int64_t)s * T + t) * cstride];
                         }
-                        bad |= step_tet<SA, kReact>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o, &heavy,
-                                                    err, tstride, use_packed, pre);
+                        light = step_is_light<SA, kReact>(d.m, mp, period, tau_kf, d.seed, t, S, N);
+                    }
+                    const unsigned slow_mask = __ballot_sync(kAll, live && !light);
+                    if (live && !light) slowq[(threadIdx.x >> 5) * 64 + n_slow + __popc(slow_mask & lane_lt)] = t;
+                    n_slow += __popc(slow_mask);
+                    if (light) {
+#pragma unroll
+                        for (int s = 0; s < SA; ++s) {
+                            if (s >= S) break;
+                            Ncur[((int64_t)s * T + t) * cstride] = 0;
+                        }
+                        bad |= step_tet<SA, false, false>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o,
+                                                          &heavy, err, tstride, use_packed, pre);
                     }
                     warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride, use_packed, pre);
-                    if (!live) continue;
-                    const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
-                    bool keep = kReact && zero_order_on(d, mp, t);
-                    bool send[4] = {false, false, false, false};
-#pragma unroll
-                    for (int s = 0; s < SA; ++s) {
-                        if (s >= S) break;
-                        int32_t* Ns = Nnext + (int64_t)s * T * cstride;
-                        if (N[s] > 0) {
-                            if (exact) {
-                                const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
-                                if (old > 2147483647 - N[s]) bad |= kErrOverflow;
-                            } else {
-                                atomicAdd(Ns + (int64_t)t * cstride, N[s]);
-                            }
-                            keep = true;
-                        }
-                        const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            if (ov[f] <= 0) continue;
-                            if (nbr[f] < 0) { bad |= kErrNegative; continue; }
-                            int32_t* dst = Ns + (int64_t)(nbr[f] >> 2) * cstride;
-                            if (exact) {
-                                const int32_t old = atomicAdd(dst, ov[f]);
-                                if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
-                            } else {
-                                atomicAdd(dst, ov[f]);
-                            }
-                            send[f] = true;
-                        }
+                    if (light) scatter(t, sr, N, o);
+                    if (n_slow >= 32) {
+                        __syncwarp();
+                        slow_round(32);
+                        // move the rest (fewer than 32) to the front
+                        const int rest = n_slow - 32;
+                        const int32_t moved = lane < rest ? slowq[(threadIdx.x >> 5) * 64 + 32 + lane] : 0;
+                        __syncwarp();
+                        if (lane < rest) slowq[(threadIdx.x >> 5) * 64 + lane] = moved;
+                        __syncwarp();
+                        n_slow = rest;
                     }
-                    if (more) {
-                        if (keep) atomicOr(word_ptr(r ^ 1, t >> 5), 1u << (t & 31));
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            if (!send[f]) continue;
-                            const int u = nbr[f] >> 2;
-                            atomicOr(word_ptr(r ^ 1, u >> 5), 1u << (u & 31));
-                        }
-                    }
+                }
+                if (n_slow > 0) {
+                    __syncwarp();
+                    slow_round(n_slow);
                 }
                 __syncwarp();   // wb is rewritten by the next group
             }

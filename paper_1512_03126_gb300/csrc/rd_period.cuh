@@ -278,6 +278,39 @@ __device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, 
 }
 
 
+// Whether some reaction with k > 0 that is on in the tet has its reactants.
+template <int SA>
+__device__ __forceinline__ bool reaction_possible(const ModelParams& mp, const int32_t* N, uint32_t on) {
+    bool possible = false;
+    for (int r = 0; r < mp.R && !possible; ++r) {
+        if (!((on >> r) & 1u)) continue;
+        int ra = mp.rs1[r], rb = mp.rs2[r];
+        int32_t na = ra < 0 ? 1 : pick<SA>(N, ra);
+        int32_t nb = rb < 0 ? 1 : pick<SA>(N, rb);
+        possible = ra < 0 || (rb < 0 ? na > 0 : (ra == rb ? na > 1 : (na > 0 && nb > 0)));
+    }
+    return possible;
+}
+
+// True when step_tet would run neither non-inlined sampler for this tet:
+// every count below kMoleculeCut and, with reactions, no event possible or
+// one proved impossible by the single-precision test.  Such a tet gives the
+// same result through step_tet<SA, false, false> (nothing touched by
+// reactions; only the per-molecule draws).
+template <int SA, bool kReact>
+__device__ __forceinline__ bool step_is_light(const DevMesh& m, const ModelParams& mp, uint32_t period,
+                                              float tau_kf, uint64_t seed, int t, int S, const int32_t* N) {
+#pragma unroll
+    for (int sp = 0; sp < SA; ++sp) {
+        if (sp >= S) break;
+        if (N[sp] >= kMoleculeCut) return false;
+    }
+    if (!kReact) return true;
+    const uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
+    if (!reaction_possible<SA>(mp, N, on)) return true;
+    return surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, t);
+}
+
 // Steps 2 and 3 of one period for one tet, given its counts N after the
 // previous period's transfers: the reaction phase (skipped when no reaction
 // can fire or the single-precision test proves that none fires), then the
@@ -286,7 +319,9 @@ __device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, 
 // species whose bit is set in *heavy: those (untouched, 10 <= N < 4096) are
 // left for warp_split, which the whole warp must call next.  Returns error
 // bits.  With has_pre, `pre` holds species 0's thresholds, already loaded.
-template <int SA, bool kReact>
+// With kCalls = false the non-inlined samplers (react_tet, diffuse) are left
+// out: the caller must have checked step_is_light first.
+template <int SA, bool kReact, bool kCalls = true>
 __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams& mp, uint32_t period, double tau_k,
                                              float tau_kf, uint64_t seed, const uint4* __restrict__ thr, int t,
                                              int S, int32_t* N, int4* o, uint32_t* heavy, uint32_t* err,
@@ -297,16 +332,9 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
     uint32_t touched = 0;
     double occ[SA];
     int64_t nmid[SA];
-    if (kReact) {
+    if (kReact && kCalls) {
         uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
-        bool possible = false;
-        for (int r = 0; r < mp.R && !possible; ++r) {
-            if (!((on >> r) & 1u)) continue;
-            int ra = mp.rs1[r], rb = mp.rs2[r];
-            int32_t na = ra < 0 ? 1 : pick<SA>(N, ra);
-            int32_t nb = rb < 0 ? 1 : pick<SA>(N, rb);
-            possible = ra < 0 || (rb < 0 ? na > 0 : (ra == rb ? na > 1 : (na > 0 && nb > 0)));
-        }
+        const bool possible = reaction_possible<SA>(mp, N, on);
         if (possible && !surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, t)) {
             int64_t N64[SA];
             double tl[SA];
@@ -343,7 +371,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
                 *heavy |= 1u << sp;        // drawn by the whole warp (warp_split)
                 o[sp] = x;
                 continue;
-            } else {
+            } else if (kCalls) {
                 x = diffuse(m.G, m.g, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
                             tch ? nmid[sp] : (int64_t)Nt, mp.rule,
                             (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
