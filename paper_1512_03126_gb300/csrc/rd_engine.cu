@@ -106,6 +106,298 @@ inline int64_t shared_bits_words(int64_t W, int kc) {
     return 2 * rows * kRowStride;
 }
 
+constexpr int kWarps = kRunBlock / 32;
+constexpr int kQueue = 64;   // deferred tets per warp
+
+// Shared memory of the engine kernel, at file scope so that the period
+// functions below address it directly.
+__shared__ int32_t s_item;                          // work-item index (first CTA of the cluster)
+__shared__ uint32_t s_total[2];                     // molecule total of a reaction-free simulation; [1]: too large
+__shared__ uint32_t s_wbuf[kWarps][kGroup * 32];    // per warp: the bitmap words of its current group
+__shared__ int32_t s_slowq[kWarps][kQueue];         // per warp: tets deferred to the rounds with the full step
+extern __shared__ uint32_t s_bits[];                // [2][rows * kRowStride]: this CTA's runs of both bitmaps
+
+// Where one period stands for one warp: the light pass stops early when the
+// warp's queue could overflow and resumes at (g0, j0) after the queue is run.
+struct LightState {
+    uint32_t bad;
+    int32_t n_slow;      // tets in the warp's queue
+    int32_t g0, j0;      // resume point (group, round)
+    int32_t finished;
+    unsigned long long done;
+};
+
+// Everything a period pass derives from the slot descriptor and the period.
+template <int kC>
+struct PeriodView {
+    int T, S, W, rw, r, tstride;
+    bool in_smem, use_packed, more, exact;
+    double tau_k;
+    float tau_kf;
+    uint32_t period;
+    const uint4* thr;
+    int32_t* Ncur;
+    int32_t* Nnext;
+    int64_t cstride;
+
+    __device__ __forceinline__ PeriodView(const SlotDesc& d, int q, int32_t dyn_words, bool exact_) {
+        constexpr int kW = kC * kWarps;
+        T = d.m.T;
+        S = d.S;
+        W = (T + 31) >> 5;
+        rw = (W + 8 * kW - 1) / (8 * kW) * kRowStride;
+        in_smem = 2 * rw <= dyn_words;
+        r = (q - d.q0) & 1;
+        const bool last = (q == d.P - 1) && d.last_short;
+        tau_k = last ? d.tau_last : d.tau;
+        tau_kf = last ? d.tau_lastf : d.tauf;
+        // thresholds: packed beside the reverse-face record (stride 2) except
+        // in a shortened last period
+        use_packed = d.packed != nullptr && !last;
+        thr = last ? d.thr_last : (use_packed ? d.packed + 1 : d.thr);
+        tstride = use_packed ? 2 : 1;
+        period = d.period0 + (uint32_t)q;
+        // counts of this period and the next: N[r] / N[r^1], or the two
+        // halves of the interleaved pairs
+        const bool inter = d.N2 != nullptr;
+        Ncur = inter ? d.N2 + r : d.N[r];
+        Nnext = inter ? d.N2 + (r ^ 1) : d.N[r ^ 1];
+        cstride = inter ? 2 : 1;
+        more = q + 1 < d.q1;
+        exact = exact_;
+    }
+
+    // Word wi of bitmap p: in the shared memory of the CTA whose warp scans
+    // it, or in global memory.
+    __device__ __forceinline__ uint32_t* word_ptr(const SlotDesc& d, int p, int wi) const {
+        constexpr int kW = kC * kWarps;
+        if (!in_smem) return d.bits[p] + wi;
+        const int run = wi >> 3;
+        const int owner = run % kW;
+        uint32_t* a = s_bits + p * rw + (run / kW) * kRowStride + (owner % kWarps) * 8 + (wi & 7);
+        if (kC == 1) return a;
+        return cooperative_groups::this_cluster().map_shared_rank(a, owner / kWarps);
+    }
+
+    // Transfer of one tet's molecules (kept and leaving) into the next
+    // counts, and its bits in the next bitmap.
+    template <int SA, bool kReact>
+    __device__ __forceinline__ uint32_t scatter(const SlotDesc& d, const ModelParams& mp, int t, const int4& sr,
+                                                const int32_t* N, const int4* o) const {
+        uint32_t bad = 0;
+        const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
+        bool keep = kReact && zero_order_on(d, mp, t);
+        bool send[4] = {false, false, false, false};
+#pragma unroll
+        for (int s = 0; s < SA; ++s) {
+            if (s >= S) break;
+            int32_t* Ns = Nnext + (int64_t)s * T * cstride;
+            if (N[s] > 0) {
+                if (exact) {
+                    const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
+                    if (old > 2147483647 - N[s]) bad |= kErrOverflow;
+                } else {
+                    red_add(Ns + (int64_t)t * cstride, N[s]);
+                }
+                keep = true;
+            }
+            const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (ov[f] <= 0) continue;
+                if (nbr[f] < 0) { bad |= kErrNegative; continue; }
+                int32_t* dst = Ns + (int64_t)(nbr[f] >> 2) * cstride;
+                if (exact) {
+                    const int32_t old = atomicAdd(dst, ov[f]);
+                    if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
+                } else {
+                    red_add(dst, ov[f]);
+                }
+                send[f] = true;
+            }
+        }
+        if (more) {
+            if (keep) atomicOr(word_ptr(d, r ^ 1, t >> 5), 1u << (t & 31));
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (!send[f]) continue;
+                const int u = nbr[f] >> 2;
+                atomicOr(word_ptr(d, r ^ 1, u >> 5), 1u << (u & 31));
+            }
+        }
+        return bad;
+    }
+};
+
+// The light pass of one period for one warp: scan the warp's bitmap words,
+// run every tet that needs no non-inlined sampler (step_is_light) with the
+// call-free step, and queue the others.  Kept out of line, and free of calls,
+// so that the compiler allocates its registers without the double-precision
+// samplers' demands (with them in the same loop nest it spills the round's
+// live values to local memory, which cost 5x in time).  Returns early, with
+// a resume point, when the next round could overflow the queue.
+template <int SA, bool kReact, int kC>
+__device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, const ModelParams* __restrict__ mpp,
+                                              int q, int32_t dyn_words, bool exact, uint32_t* err, bool resuming,
+                                              int g_start, int j_start) {
+    constexpr unsigned kAll = 0xffffffffu;
+    constexpr int kW = kC * kWarps;
+    const SlotDesc& d = *dp;
+    const ModelParams& mp = *mpp;
+    const PeriodView<kC> v(d, q, dyn_words, exact);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int rank = kC > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+    const int gw = rank * kWarps + warp;
+    const unsigned lane_lt = (1u << lane) - 1u;
+    uint32_t* wb = s_wbuf[warp];
+    int32_t* slowq = s_slowq[warp];
+    // this warp's runs of the current bitmap (row stride kRowStride in
+    // shared memory) or the global bitmap
+    uint32_t* bcur = v.in_smem ? s_bits + v.r * v.rw + warp * 8 : d.bits[v.r];
+    LightState st{0u, 0, 0, 0, 1, 0ull};
+    for (int g0 = g_start; g0 < v.W; g0 += kGroup * 32 * kW) {
+        // a resumed group's words are already in wb (and cleared in the bitmap)
+        const bool resume = resuming && g0 == g_start;
+        if (!resume) {
+            uint32_t wds[kGroup];
+#pragma unroll
+            for (int kk = 0; kk < kGroup; ++kk) {
+                const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
+                const int li = v.in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
+                wds[kk] = wi < v.W ? bcur[li] : 0u;
+            }
+#pragma unroll
+            for (int kk = 0; kk < kGroup; ++kk) {
+                const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
+                const int li = v.in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
+                if (wds[kk]) bcur[li] = 0u;
+                wb[kk * 32 + lane] = wds[kk];
+            }
+            __syncwarp();
+        }
+        uint32_t c = 0;
+#pragma unroll
+        for (int kk = 0; kk < kGroup; ++kk) c += (uint32_t)__popc(wb[kk * 32 + lane]);
+        uint32_t inc = c;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const uint32_t y = __shfl_up_sync(kAll, inc, dd);
+            if (lane >= dd) inc += y;
+        }
+        const uint32_t n_act = __shfl_sync(kAll, inc, 31);
+        const uint32_t before = inc - c;
+        if (!resume) st.done += n_act;
+        for (uint32_t j0 = resume ? (uint32_t)j_start : 0u; j0 < n_act; j0 += 32) {
+            const uint32_t j = j0 + (uint32_t)lane;
+            const bool live = j < n_act;
+            const uint32_t jj = live ? j : n_act - 1u;
+            const int own = owner_lane(before, jj);
+            uint32_t rel = jj - __shfl_sync(kAll, before, own);
+            // the owner's word that holds bit number rel
+            int kw = 0;
+            uint32_t ww = 0;
+            bool found = false;
+#pragma unroll
+            for (int kk = 0; kk < kGroup; ++kk) {
+                const uint32_t w = wb[kk * 32 + own];
+                const uint32_t pc = (uint32_t)__popc(w);
+                if (!found) {
+                    if (rel < pc) {
+                        found = true;
+                        kw = kk;
+                        ww = w;
+                    } else {
+                        rel -= pc;
+                    }
+                }
+            }
+            const int t = live ? (g0 + ((kw * 4 + (own >> 3)) * kW + gw) * 8 + (own & 7)) * 32 + select_bit(ww, rel)
+                               : 0;
+            uint32_t heavy = 0;
+            int32_t N[SA];
+            int4 o[SA];
+            int4 sr = make_int4(-1, -1, -1, -1);
+            uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+            bool light = false;
+            if (live) {
+                // the tet's record and counts, loaded together
+                sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
+                if (v.use_packed) pre = d.packed[2 * t + 1];
+#pragma unroll
+                for (int s = 0; s < SA; ++s) {
+                    if (s >= v.S) break;
+                    N[s] = v.Ncur[((int64_t)s * v.T + t) * v.cstride];
+                }
+                light = step_is_light<SA, kReact>(d.m, mp, v.period, v.tau_kf, d.seed, t, v.S, N);
+            }
+            const unsigned slow_mask = __ballot_sync(kAll, live && !light);
+            if (st.n_slow + __popc(slow_mask) > kQueue) {
+                // no side effect of this round has happened yet: stop here
+                st.g0 = g0;
+                st.j0 = (int)j0;
+                st.finished = 0;
+                __syncwarp();   // the queue is read by other lanes next
+                return st;
+            }
+            if (live && !light) slowq[st.n_slow + __popc(slow_mask & lane_lt)] = t;
+            st.n_slow += __popc(slow_mask);
+            if (light) {
+#pragma unroll
+                for (int s = 0; s < SA; ++s) {
+                    if (s >= v.S) break;
+                    v.Ncur[((int64_t)s * v.T + t) * v.cstride] = 0;
+                }
+                st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N,
+                                                     o, &heavy, err, v.tstride, v.use_packed, pre);
+            }
+            warp_split<SA>(heavy, d.seed, v.period, t, v.thr, v.T, N, o, v.tstride, v.use_packed, pre);
+            if (light) st.bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
+        }
+        __syncwarp();   // wb is rewritten by the next group
+    }
+    return st;
+}
+
+// The deferred tets of one warp's queue (n of them), in rounds of 32, with
+// the full per-tet step: reactions and the non-inlined samplers.
+template <int SA, bool kReact, int kC>
+__device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, const ModelParams* __restrict__ mpp, int q,
+                                           int32_t dyn_words, bool exact, uint32_t* err, int n) {
+    const SlotDesc& d = *dp;
+    const ModelParams& mp = *mpp;
+    const PeriodView<kC> v(d, q, dyn_words, exact);
+    const int lane = threadIdx.x & 31;
+    const int32_t* slowq = s_slowq[threadIdx.x >> 5];
+    uint32_t bad = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const bool live = k0 + lane < n;
+        const int t = live ? slowq[k0 + lane] : 0;
+        uint32_t heavy = 0;
+        int32_t N[SA];
+        int4 o[SA];
+        int4 sr = make_int4(-1, -1, -1, -1);
+        uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+        if (live) {
+            sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
+            if (v.use_packed) pre = d.packed[2 * t + 1];
+#pragma unroll
+            for (int s = 0; s < SA; ++s) {
+                if (s >= v.S) break;
+                int32_t* p = v.Ncur + ((int64_t)s * v.T + t) * v.cstride;
+                N[s] = *p;
+                *p = 0;
+            }
+            bad |= step_tet<SA, kReact, true>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
+                                              &heavy, err, v.tstride, v.use_packed, pre);
+        }
+        warp_split<SA>(heavy, d.seed, v.period, t, v.thr, v.T, N, o, v.tstride, v.use_packed, pre);
+        if (live) bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
+    }
+    __syncwarp();   // the queue is refilled by the next light pass
+    return bad;
+}
+
 // One simulation per cluster of kC CTAs (kC = 1: per CTA).  The cluster's
 // first CTA owns the work-item index; the others read it through distributed
 // shared memory.  cluster.sync() (a hardware barrier) separates periods.
@@ -136,25 +428,16 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
              int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed, int32_t dyn_words) {
     namespace cg = cooperative_groups;
     constexpr unsigned kAll = 0xffffffffu;
-    constexpr int kWarps = kRunBlock / 32;
     constexpr int kW = kC * kWarps;   // warps per simulation
-    __shared__ int32_t item_s;
-    __shared__ uint32_t total_s[2];   // molecules of a reaction-free simulation; [1] != 0: above 2^31-1
-    __shared__ uint32_t wbuf[kWarps][kGroup * 32];
-    __shared__ int32_t slowq[kWarps * 64];   // per warp: tets deferred to the rounds with calls
-    extern __shared__ uint32_t sbits[];   // [2][rows * kRowStride]: this CTA's runs of both bitmaps
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
-    int32_t* item = kC > 1 ? cluster.map_shared_rank(&item_s, 0) : &item_s;
-    uint32_t* total = kC > 1 ? cluster.map_shared_rank(&total_s[0], 0) : &total_s[0];
+    int32_t* item = kC > 1 ? cluster.map_shared_rank(&s_item, 0) : &s_item;
+    uint32_t* total = kC > 1 ? cluster.map_shared_rank(&s_total[0], 0) : &s_total[0];
     auto csync = [&]() {
         if (kC > 1) cluster.sync();
         else __syncthreads();
     };
     const int lane = threadIdx.x & 31;
-    const int gw = rank * kWarps + (threadIdx.x >> 5);
-    const unsigned lane_lt = (1u << lane) - 1u;
-    uint32_t* wb = wbuf[threadIdx.x >> 5];
     unsigned long long done = 0;
     for (;;) {
         csync();
@@ -177,21 +460,10 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         const int W = (T + 31) >> 5;
         const bool inter = d.N2 != nullptr;   // one species, interleaved counts
         const bool conserved = mp.R == 0;     // molecules are only moved
-        const int rw = (W + 8 * kW - 1) / (8 * kW) * kRowStride;
-        const bool in_smem = 2 * rw <= dyn_words;
-        // word wi of bitmap p: in the shared memory of the CTA whose warp
-        // scans it, or in global memory
-        auto word_ptr = [&](int p, int wi) -> uint32_t* {
-            if (!in_smem) return d.bits[p] + wi;
-            const int run = wi >> 3;
-            const int owner = run % kW;
-            uint32_t* a = sbits + p * rw + (run / kW) * kRowStride + (owner % kWarps) * 8 + (wi & 7);
-            if (kC == 1) return a;
-            return cluster.map_shared_rank(a, owner / kWarps);
-        };
+        const PeriodView<kC> v0(d, d.q0, dyn_words, true);
         uint32_t bad = 0;
-        if (in_smem)
-            for (int i = threadIdx.x; i < rw; i += kRunBlock) sbits[rw + i] = 0u;   // bitmap 1 starts empty
+        if (v0.in_smem)
+            for (int i = threadIdx.x; i < v0.rw; i += kRunBlock) s_bits[v0.rw + i] = 0u;   // bitmap 1 starts empty
         // initial bitmap: occupied tets and tets with a zero-order reaction on
         // (whole words, written by the first lane of each 32-tet run); and the
         // molecule total of a reaction-free simulation
@@ -209,7 +481,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                 }
             }
             const uint32_t word = __ballot_sync(kAll, occ);
-            if (lane == 0 && (t >> 5) < W) *word_ptr(0, t >> 5) = word;
+            if (lane == 0 && (t >> 5) < W) *v0.word_ptr(d, 0, t >> 5) = word;
         }
         if (conserved) {
 #pragma unroll
@@ -225,206 +497,21 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         }
         bool exact = true;
         for (int q = d.q0; q < d.q1; ++q) {
-            const int r = (q - d.q0) & 1;
             csync();   // the previous period's adds and bits are complete
             if (q == d.q0) exact = !conserved || total[1] != 0u;
-            const bool last = (q == d.P - 1) && d.last_short;
-            const double tau_k = last ? d.tau_last : d.tau;
-            const float tau_kf = last ? d.tau_lastf : d.tauf;
-            // thresholds: packed beside the reverse-face record (stride 2) except
-            // in a shortened last period
-            const bool use_packed = d.packed != nullptr && !last;
-            const uint4* thr = last ? d.thr_last : (use_packed ? d.packed + 1 : d.thr);
-            const int tstride = use_packed ? 2 : 1;
-            const uint32_t period = d.period0 + (uint32_t)q;
-            // counts of this period and the next: N[r] / N[r^1], or the two
-            // halves of the interleaved pairs
-            int32_t* Ncur = inter ? d.N2 + r : d.N[r];
-            int32_t* Nnext = inter ? d.N2 + (r ^ 1) : d.N[r ^ 1];
-            const int64_t cstride = inter ? 2 : 1;
-            // this warp's runs of the current bitmap (row stride kRowStride in
-            // shared memory) or the global bitmap
-            uint32_t* bcur = in_smem ? sbits + r * rw + (threadIdx.x >> 5) * 8 : d.bits[r];
-            const bool more = q + 1 < d.q1;
-            // Transfer of one tet's molecules (kept and leaving) into the next
-            // counts, and its bits in the next bitmap.
-            auto scatter = [&](int t, const int4& sr, const int32_t* N, const int4* o) {
-                const int nbr[4] = {sr.x, sr.y, sr.z, sr.w};
-                bool keep = kReact && zero_order_on(d, mp, t);
-                bool send[4] = {false, false, false, false};
-#pragma unroll
-                for (int s = 0; s < SA; ++s) {
-                    if (s >= S) break;
-                    int32_t* Ns = Nnext + (int64_t)s * T * cstride;
-                    if (N[s] > 0) {
-                        if (exact) {
-                            const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
-                            if (old > 2147483647 - N[s]) bad |= kErrOverflow;
-                        } else {
-                            red_add(Ns + (int64_t)t * cstride, N[s]);
-                        }
-                        keep = true;
-                    }
-                    const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        if (ov[f] <= 0) continue;
-                        if (nbr[f] < 0) { bad |= kErrNegative; continue; }
-                        int32_t* dst = Ns + (int64_t)(nbr[f] >> 2) * cstride;
-                        if (exact) {
-                            const int32_t old = atomicAdd(dst, ov[f]);
-                            if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
-                        } else {
-                            red_add(dst, ov[f]);
-                        }
-                        send[f] = true;
-                    }
-                }
-                if (more) {
-                    if (keep) atomicOr(word_ptr(r ^ 1, t >> 5), 1u << (t & 31));
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        if (!send[f]) continue;
-                        const int u = nbr[f] >> 2;
-                        atomicOr(word_ptr(r ^ 1, u >> 5), 1u << (u & 31));
-                    }
-                }
-            };
-            // One round over the first n (<= 32) deferred tets of this warp's
-            // queue, with the full per-tet step (reactions and the
-            // non-inlined samplers).  The whole warp calls it.
-            auto slow_round = [&](int n) {
-                const bool live = lane < n;
-                const int t = live ? slowq[(threadIdx.x >> 5) * 64 + lane] : 0;
-                uint32_t heavy = 0;
-                int32_t N[SA];
-                int4 o[SA];
-                int4 sr = make_int4(-1, -1, -1, -1);
-                uint4 pre = make_uint4(0u, 0u, 0u, 0u);
-                if (live) {
-                    sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
-                    if (use_packed) pre = d.packed[2 * t + 1];
-#pragma unroll
-                    for (int s = 0; s < SA; ++s) {
-                        if (s >= S) break;
-                        int32_t* p = Ncur + ((int64_t)s * T + t) * cstride;
-                        N[s] = *p;
-                        *p = 0;
-                    }
-                    bad |= step_tet<SA, kReact, true>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o, &heavy,
-                                                      err, tstride, use_packed, pre);
-                }
-                warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride, use_packed, pre);
-                if (live) scatter(t, sr, N, o);
-            };
-            for (int g0 = 0; g0 < W; g0 += kGroup * 32 * kW) {
-                uint32_t wds[kGroup];
-#pragma unroll
-                for (int kk = 0; kk < kGroup; ++kk) {
-                    const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
-                    const int li = in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
-                    wds[kk] = wi < W ? bcur[li] : 0u;
-                }
-                uint32_t c = 0;
-#pragma unroll
-                for (int kk = 0; kk < kGroup; ++kk) {
-                    const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
-                    const int li = in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
-                    if (wds[kk]) bcur[li] = 0u;
-                    wb[kk * 32 + lane] = wds[kk];
-                    c += (uint32_t)__popc(wds[kk]);
-                }
-                __syncwarp();
-                uint32_t inc = c;
-#pragma unroll
-                for (int dd = 1; dd < 32; dd <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kAll, inc, dd);
-                    if (lane >= dd) inc += y;
-                }
-                const uint32_t n_act = __shfl_sync(kAll, inc, 31);
-                const uint32_t before = inc - c;
-                done += n_act;
-                // Entries whose tet needs a non-inlined sampler (a count of
-                // kMoleculeCut or more, or a reaction event) wait in the warp's
-                // queue and run in rounds of their own, so that the common
-                // round holds no call (a call there makes the compiler spill
-                // the round's live registers to local memory).
-                int n_slow = 0;                       // warp-uniform
-                for (uint32_t j0 = 0; j0 < n_act; j0 += 32) {
-                    const uint32_t j = j0 + (uint32_t)lane;
-                    const bool live = j < n_act;
-                    const uint32_t jj = live ? j : n_act - 1u;
-                    const int own = owner_lane(before, jj);
-                    uint32_t rel = jj - __shfl_sync(kAll, before, own);
-                    // the owner's word that holds bit number rel
-                    int kw = 0;
-                    uint32_t ww = 0;
-                    bool found = false;
-#pragma unroll
-                    for (int kk = 0; kk < kGroup; ++kk) {
-                        const uint32_t w = wb[kk * 32 + own];
-                        const uint32_t pc = (uint32_t)__popc(w);
-                        if (!found) {
-                            if (rel < pc) {
-                                found = true;
-                                kw = kk;
-                                ww = w;
-                            } else {
-                                rel -= pc;
-                            }
-                        }
-                    }
-                    const int t = live ? (g0 + ((kw * 4 + (own >> 3)) * kW + gw) * 8 + (own & 7)) * 32 +
-                                             select_bit(ww, rel)
-                                       : 0;
-                    uint32_t heavy = 0;
-                    int32_t N[SA];
-                    int4 o[SA];
-                    int4 sr = make_int4(-1, -1, -1, -1);
-                    uint4 pre = make_uint4(0u, 0u, 0u, 0u);
-                    bool light = false;
-                    if (live) {
-                        // the tet's record and counts, loaded together
-                        sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
-                        if (use_packed) pre = d.packed[2 * t + 1];
-#pragma unroll
-                        for (int s = 0; s < SA; ++s) {
-                            if (s >= S) break;
-                            N[s] = Ncur[((int64_t)s * T + t) * cstride];
-                        }
-                        light = step_is_light<SA, kReact>(d.m, mp, period, tau_kf, d.seed, t, S, N);
-                    }
-                    const unsigned slow_mask = __ballot_sync(kAll, live && !light);
-                    if (live && !light) slowq[(threadIdx.x >> 5) * 64 + n_slow + __popc(slow_mask & lane_lt)] = t;
-                    n_slow += __popc(slow_mask);
-                    if (light) {
-#pragma unroll
-                        for (int s = 0; s < SA; ++s) {
-                            if (s >= S) break;
-                            Ncur[((int64_t)s * T + t) * cstride] = 0;
-                        }
-                        bad |= step_tet<SA, false, false>(d.m, mp, period, tau_k, tau_kf, d.seed, thr, t, S, N, o,
-                                                          &heavy, err, tstride, use_packed, pre);
-                    }
-                    warp_split<SA>(heavy, d.seed, period, t, thr, T, N, o, tstride, use_packed, pre);
-                    if (light) scatter(t, sr, N, o);
-                    if (n_slow >= 32) {
-                        __syncwarp();
-                        slow_round(32);
-                        // move the rest (fewer than 32) to the front
-                        const int rest = n_slow - 32;
-                        const int32_t moved = lane < rest ? slowq[(threadIdx.x >> 5) * 64 + 32 + lane] : 0;
-                        __syncwarp();
-                        if (lane < rest) slowq[(threadIdx.x >> 5) * 64 + lane] = moved;
-                        __syncwarp();
-                        n_slow = rest;
-                    }
-                }
-                if (n_slow > 0) {
-                    __syncwarp();
-                    slow_round(n_slow);
-                }
-                __syncwarp();   // wb is rewritten by the next group
+            int g0 = 0, j0 = 0;
+            bool resuming = false;
+            for (;;) {
+                const LightState st = light_pass<SA, kReact, kC>(descs + slot, mps + slot, q, dyn_words, exact, err,
+                                                                 resuming, g0, j0);
+                bad |= st.bad;
+                done += st.done;
+                if (st.n_slow > 0) bad |= slow_pass<SA, kReact, kC>(descs + slot, mps + slot, q, dyn_words, exact, err,
+                                                                    st.n_slow);
+                if (st.finished) break;
+                g0 = st.g0;
+                j0 = st.j0;
+                resuming = true;
             }
         }
         csync();   // every add of the slice is complete

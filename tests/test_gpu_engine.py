@@ -183,3 +183,24 @@ def test_full_size_ensemble_and_requests_in_one_launch(rd):
     finally:
         for s in sims:
             s.close()
+
+
+def test_deferred_queue_overflow_and_resume(rd, oracle):
+    """A dense reaction workload (most tets have a reaction event in every
+    period, so most tets take the deferred full step): with one CTA per
+    simulation each warp defers far more than its 64-entry queue per period,
+    so the light pass stops and resumes many times."""
+    m = I.cube(8, 1e-6, 0.2, 21)
+    n = I.molecules(400e-6, 1e-18)
+    w = I.Workload("abc_dense", m, I.abc_model(), I.place_by_volume(m, [n, n, n // 4], 6), 2e-3, 5)
+    ref = _oracle(oracle, w)
+    for cluster in (1, 4):
+        with rd.Simulation(w.mesh, w.model, w.counts) as s:
+            e = rd.rdsplit_engine_create(1, m.n_tets)
+            try:
+                rd.rdsplit_engine_set_concurrency(e, 1, cluster)
+                rd.rdsplit_engine_add(e, s.h, w.t_end, w.seed)
+                rd.rdsplit_engine_step(e, 1 << 30)
+            finally:
+                rd.rdsplit_engine_destroy(e)
+            assert np.array_equal(s.counts(), ref), cluster
