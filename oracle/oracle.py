@@ -46,6 +46,10 @@ def lib():
         L.orc_run.restype = C.c_int
         L.orc_run_rule.argtypes = L.orc_run.argtypes + [C.c_int32]
         L.orc_run_rule.restype = C.c_int
+        L.orc_run_opts.argtypes = L.orc_run.argtypes + [C.c_int32, C.c_int32]
+        L.orc_run_opts.restype = C.c_int
+        L.orc_tau_outliers.argtypes = L.orc_tau.argtypes + [C.c_int32]
+        L.orc_tau_outliers.restype = C.c_double
         L.orc_issa_run.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _i32p, C.c_double,
                                    C.c_uint64]
@@ -128,8 +132,13 @@ def _model_arrays(model):
     return S, R, D, lhs, rhs, k, mask
 
 
-def tau(mesh, model) -> float:
+def tau(mesh, model, outliers: int = 0) -> float:
+    """tau of Algorithm 1; with outliers = k > 0, taken from the (k+1)-th
+    fastest tet (the outlier option of Sec. II.A)."""
     S, R, D, *_ = _model_arrays(model)
+    if outliers:
+        return lib().orc_tau_outliers(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D,
+                                      float(model.tau_scale), int(outliers))
     return lib().orc_tau(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D,
                          float(model.tau_scale))
 
@@ -145,21 +154,22 @@ RULE_MID = 2    # N(tau_k / 2): the half-step ("median") reading
 
 
 def run(mesh, model, counts, t_end: float, seed: int, t0: float = 0.0, period0: int = 0,
-        max_periods: int = -1, rule: int = RULE_MEAN):
+        max_periods: int = -1, rule: int = RULE_MEAN, outliers: int = 0):
     """Algorithm 1 from ``t0`` towards ``t_end`` (at most ``max_periods``
-    periods) with the given transfer rule.  Returns (counts [T][S] int32, t,
+    periods) with the given transfer rule and tau taken from the
+    (outliers + 1)-th fastest tet.  Returns (counts [T][S] int32, t,
     period)."""
     S, R, D, lhs, rhs, k, mask = _model_arrays(model)
     c = np.ascontiguousarray(counts, np.int32).copy()
     assert c.shape == (mesh.n_tets, S)
     t = C.c_double(t0)
     p = C.c_int64(period0)
-    rc = lib().orc_run_rule(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
+    rc = lib().orc_run_opts(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, R,
                             lhs.ctypes.data, rhs.ctypes.data, k.ctypes.data, _ptr(mask),
                             float(model.tau_scale), c, C.byref(t), C.byref(p), float(t_end),
-                            int(seed), int(max_periods), int(rule))
+                            int(seed), int(max_periods), int(rule), int(outliers))
     if rc != 0:
-        raise OracleError(f"orc_run_rule failed with code {rc}")
+        raise OracleError(f"orc_run_opts failed with code {rc}")
     return c, t.value, p.value
 
 

@@ -17,6 +17,7 @@
 //   key     = (seed & 0xffffffff, seed >> 32)
 //   counter = (block, tet, period, purpose << 16 | species)
 // The words of a stream are consumed in order, four per block.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -266,6 +267,7 @@ struct Problem {
     const uint8_t* mask;     // [R][T] or null
     double tau_scale;
     int rule;                // transfer rule: kRuleMean, kRuleEnd or kRuleMid
+    int outliers;            // fastest tets left out of the choice of tau (Sec. II.A)
 };
 
 // Which count of a period the diffusion draw of Step 3.2 uses (Sec. II.C).
@@ -284,6 +286,10 @@ const int kRuleMid = 2;
 //   G[t] = g0 + g1 + g2 + g3 (in that order) so that the local diffusion rate
 //   of species s is d_st = D_s * G[t] and the face weights are w_f = g_f / G;
 //   tau = tau_scale / max over (s, t) of d_st.
+// With P.outliers = k > 0 (the outlier option of Sec. II.A: leave the few
+// tets with the highest zeta out of the choice of tau), tau = tau_scale /
+// d_(k+1), d_(j) the j-th largest of the per-tet rates d_t = max_s d_st; the
+// k faster tets then have tau * d_t > 1 and their zeta is capped at 1.
 struct Geometry {
     std::vector<double> g, G;
     double tau;
@@ -293,7 +299,7 @@ Geometry setup_geometry(const Problem& P) {
     Geometry geo;
     geo.g.assign((size_t)P.T * 4, 0.0);
     geo.G.assign(P.T, 0.0);
-    double dmax = 0.0;
+    std::vector<double> dt(P.T, 0.0);
     for (int t = 0; t < P.T; ++t) {
         double Gt = 0.0;
         for (int f = 0; f < 4; ++f) {
@@ -305,10 +311,13 @@ Geometry setup_geometry(const Problem& P) {
         geo.G[t] = Gt;
         for (int s = 0; s < P.S; ++s) {
             double d = P.D[s] * Gt;
-            if (d > dmax) dmax = d;
+            if (d > dt[t]) dt[t] = d;
         }
     }
-    geo.tau = dmax > 0.0 ? P.tau_scale / dmax : std::numeric_limits<double>::infinity();
+    // the (outliers + 1)-th largest per-tet rate
+    std::sort(dt.begin(), dt.end(), [](double a, double b) { return a > b; });
+    const double dsel = dt[P.outliers];
+    geo.tau = dsel > 0.0 ? P.tau_scale / dsel : std::numeric_limits<double>::infinity();
     return geo;
 }
 
@@ -520,7 +529,16 @@ void orc_binomial_many(uint64_t seed, uint32_t period, int64_t n, double p, int6
 // species diffuses.
 double orc_tau(int32_t T, const int32_t* adj, const double* vol, const double* area,
                const double* dist, int32_t S, const double* D, double tau_scale) {
-    Problem P{T, S, 0, adj, vol, area, dist, D, nullptr, nullptr, nullptr, nullptr, tau_scale, kRuleMean};
+    Problem P{T, S, 0, adj, vol, area, dist, D, nullptr, nullptr, nullptr, nullptr, tau_scale, kRuleMean, 0};
+    return setup_geometry(P).tau;
+}
+
+// tau with the `outliers` fastest tets left out of its choice (Sec. II.A);
+// NaN for outliers outside [0, T).
+double orc_tau_outliers(int32_t T, const int32_t* adj, const double* vol, const double* area,
+                        const double* dist, int32_t S, const double* D, double tau_scale, int32_t outliers) {
+    if (outliers < 0 || outliers >= T) return std::numeric_limits<double>::quiet_NaN();
+    Problem P{T, S, 0, adj, vol, area, dist, D, nullptr, nullptr, nullptr, nullptr, tau_scale, kRuleMean, outliers};
     return setup_geometry(P).tau;
 }
 
@@ -531,14 +549,16 @@ double orc_tau(int32_t T, const int32_t* adj, const double* vol, const double* a
 // -3 int32 overflow.
 // `rule` selects the count the diffusion draw uses (kRuleMean, the method;
 // kRuleEnd or kRuleMid, the comparison rules of Sec. II.C and III.B).
-int orc_run_rule(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
+// `outliers` > 0 takes tau from the (outliers + 1)-th fastest tet (Sec. II.A).
+int orc_run_opts(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
                  int32_t S, const double* D, int32_t R, const int32_t* lhs, const int32_t* rhs,
                  const double* k, const uint8_t* mask, double tau_scale,
                  int32_t* counts, double* t_io, int64_t* period_io, double t_end, uint64_t seed,
-                 int64_t max_periods, int32_t rule) {
+                 int64_t max_periods, int32_t rule, int32_t outliers) {
     if (T <= 0 || S <= 0 || S > kMaxSpecies || R < 0 || R > kMaxReactions) return -1;
     if (rule != kRuleMean && rule != kRuleEnd && rule != kRuleMid) return -1;
-    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale, rule};
+    if (outliers < 0 || outliers >= T) return -1;
+    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale, rule, outliers};
     Geometry geo = setup_geometry(P);
     std::vector<int64_t> N((size_t)T * S), rem((size_t)T * S), out((size_t)T * S * 4);
     for (size_t i = 0; i < N.size(); ++i) N[i] = counts[i];
@@ -618,8 +638,18 @@ int orc_run(int32_t T, const int32_t* adj, const double* vol, const double* area
             const double* k, const uint8_t* mask, double tau_scale,
             int32_t* counts, double* t_io, int64_t* period_io, double t_end, uint64_t seed,
             int64_t max_periods) {
-    return orc_run_rule(T, adj, vol, area, dist, S, D, R, lhs, rhs, k, mask, tau_scale, counts, t_io, period_io,
-                        t_end, seed, max_periods, kRuleMean);
+    return orc_run_opts(T, adj, vol, area, dist, S, D, R, lhs, rhs, k, mask, tau_scale, counts, t_io, period_io,
+                        t_end, seed, max_periods, kRuleMean, 0);
+}
+
+// Algorithm 1 with a transfer rule and the default choice of tau.
+int orc_run_rule(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
+                 int32_t S, const double* D, int32_t R, const int32_t* lhs, const int32_t* rhs,
+                 const double* k, const uint8_t* mask, double tau_scale,
+                 int32_t* counts, double* t_io, int64_t* period_io, double t_end, uint64_t seed,
+                 int64_t max_periods, int32_t rule) {
+    return orc_run_opts(T, adj, vol, area, dist, S, D, R, lhs, rhs, k, mask, tau_scale, counts, t_io, period_io,
+                        t_end, seed, max_periods, rule, 0);
 }
 
 // Steps 2 and 3 of one period (reactions, then the diffusion draws) for the
@@ -635,7 +665,7 @@ int orc_period_tets(int32_t T, const int32_t* adj, const double* vol, const doub
                     int32_t* out, int32_t* rem) {
     if (T <= 0 || S <= 0 || S > kMaxSpecies || R < 0 || R > kMaxReactions) return -1;
     if (t_begin < 0 || t_end > T || t_begin > t_end) return -1;
-    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale, kRuleMean};
+    Problem P{T, S, R, adj, vol, area, dist, D, lhs, rhs, k, mask, tau_scale, kRuleMean, 0};
     Geometry geo = setup_geometry(P);
     for (int t = t_begin; t < t_end; ++t) {
         int64_t Nt[kMaxSpecies], Nmid[kMaxSpecies];

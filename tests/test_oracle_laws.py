@@ -209,6 +209,43 @@ def test_rules_agree_without_reactions(oracle):
         assert np.array_equal(oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed, rule=rule)[0], base)
 
 
+def _rates_numpy(mesh, D):
+    """Per-tet rates d_t = D * (g0 + g1 + g2 + g3), g_f = A / (V dist), in the
+    same floating-point operations as the method's setup (Sec. II.A)."""
+    inner = mesh.adj >= 0
+    g = np.where(inner, mesh.area / (mesh.vol[:, None] * np.where(inner, mesh.dist, 1.0)), 0.0)
+    G = ((g[:, 0] + g[:, 1]) + g[:, 2]) + g[:, 3]
+    return D * G
+
+
+@pytest.mark.parametrize("k", [0, 1, 5])
+def test_outlier_option_takes_tau_from_the_next_tet(oracle, k):
+    """Sec. II.A: leaving the k tets with the highest zeta out of the choice
+    of tau gives tau = tau_scale / d_(k+1), the (k+1)-th largest per-tet rate."""
+    m = I.cube(4, 1e-6, 0.2, 31)
+    model = I.diffusion_model(1e-12)
+    model.tau_scale = 0.8
+    d = np.sort(_rates_numpy(m, 1e-12))[::-1]
+    assert oracle.tau(m, model, outliers=k) == 0.8 / d[k]
+
+
+def test_outlier_tets_have_zeta_one(oracle):
+    """With the three fastest tets left out of the choice of tau, the second
+    fastest has tau * d > 1, so zeta = 1 there: every molecule leaves it in
+    one period (and some stay without the option, where zeta = d_2/d_1 < 1)."""
+    m = I.cube(4, 1e-6, 0.2, 31)
+    model = I.diffusion_model(1e-12)
+    d = _rates_numpy(m, 1e-12)
+    order = np.argsort(-d)
+    assert d[order[1]] < d[order[0]] and d[order[1]] > d[order[3]]
+    c0 = np.zeros((m.n_tets, 1), np.int32)
+    c0[order[1], 0] = 1000
+    left = oracle.run(m, model, c0, np.inf, 3, max_periods=1, outliers=3)[0]
+    assert left[order[1], 0] == 0 and left.sum() == 1000
+    kept = oracle.run(m, model, c0, np.inf, 3, max_periods=1)[0]
+    assert kept[order[1], 0] > 0
+
+
 def test_point_source_spreads_at_6Dt(oracle):
     """Volume diffusion speed (Sec. III.A): from a point source the mean
     squared displacement grows as 6 D t in 3-D (before the walls matter)."""

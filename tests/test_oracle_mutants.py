@@ -30,6 +30,10 @@ MUTANTS = {
         "    } else if (P.rule == kRuleMean && touched) {\n        Stream rs(",
         "    } else if (false) {\n        Stream rs(",
         [L.test_mean_corrected_transfer]),
+    "outlier_rank_off_by_one": (
+        "    const double dsel = dt[P.outliers];",
+        "    const double dsel = dt[P.outliers > 0 ? P.outliers - 1 : 0];",
+        [lambda o: L.test_outlier_option_takes_tau_from_the_next_tet(o, 1)]),
     "mid_rule_takes_end_count": (
         "        Nstar = Nmid;",
         "        Nstar = Nt;",
