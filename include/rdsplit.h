@@ -96,6 +96,31 @@ int rdsplit_set_model(rdsplit_mesh_t mesh, int32_t n_species, const double* D,
                       const double* k, const uint8_t* rxn_tet_mask, double tau_scale);
 
 /*
+ * Outlier option for tau (Sec. II.A): take tau = tau_scale / d_(k+1), d_(j)
+ * the j-th largest per-tet rate max_s D_s * sum_f g_tf, instead of the
+ * largest; the k fastest tets then have tau * d > 1 and run with zeta
+ * capped at 1 (every molecule there leaves each period), a small cost to
+ * accuracy that raises tau for a mesh with a few tiny tets.  k = 0 restores
+ * the default.  Needs a model; rdsplit_set_model resets k to 0.  Recomputes
+ * tau and the face thresholds on the device (a rank selection over G).
+ *   k    0 <= k < n_tets, else RDSPLIT_EINVAL
+ */
+int rdsplit_set_zeta_outliers(rdsplit_mesh_t mesh, int32_t k);
+
+/*
+ * Diagnostic (Fig. 1d): histogram of zeta_t = min(1, tau * D_max * G_t) over
+ * the tets, for the fastest species.
+ *   nbins     1 .. 2^20; bin b holds zeta in [b/nbins, (b+1)/nbins), and
+ *             zeta = 1 falls in the last bin
+ *   counts    int64 [nbins] (host), filled
+ *   mean      mean zeta over the tets, or NULL (summed with atomics: the last
+ *             bits may vary between calls)
+ *   max_zeta  largest zeta, or NULL
+ * With no diffusing species (tau infinite) every zeta is reported as 0.
+ */
+int rdsplit_zeta_histogram(rdsplit_mesh_t mesh, int32_t nbins, int64_t* counts, double* mean, double* max_zeta);
+
+/*
  * Transfer rule: which count of a period the diffusion draw of Step 3.2 uses
  * (Sec. II.C; the comparison of Sec. III.B, Fig. 7).
  *   RDSPLIT_TRANSFER_MEAN  N-bar, the mean occupancy over the period (Eq. 3);

@@ -2,6 +2,7 @@
 // argument validation, device memory, and the period loop of Algorithm 1
 // (Step 1 alignment and Step 4 time advance, arXiv:1512.03126) around the
 // kernels of rd_kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -252,6 +253,108 @@ int rdsplit_set_transfer_rule(rdsplit_mesh_t h, int32_t rule) {
     return RDSPLIT_OK;
 }
 
+int rdsplit_set_zeta_outliers(rdsplit_mesh_t h, int32_t k) {
+    const char* where = "rdsplit_set_zeta_outliers";
+    if (!h) return fail(RDSPLIT_EINVAL, "%s: NULL handle", where);
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "%s: no model attached", where);
+    if (k < 0 || k >= h->T) return fail(RDSPLIT_EINVAL, "%s: k must be in [0, n_tets)", where);
+    cudaStream_t st = h->stream;
+    unsigned long long* sel = nullptr;   // bits of the (k+1)-th largest G
+    unsigned int* cnt = nullptr;
+    int rc;
+    if ((rc = alloc_into(&sel, 1, "selection")) || (rc = alloc_into(&cnt, 1, "count"))) {
+        dev_free(sel);
+        dev_free(cnt);
+        return rc;
+    }
+    auto done = [&](int code) {
+        dev_free(sel);
+        dev_free(cnt);
+        return code;
+    };
+    unsigned long long hi = 0;
+    cudaError_t ce = cudaMemcpyAsync(&hi, h->gmax, sizeof hi, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    // largest x (as bits, G >= 0) with at least k+1 tets at or above it:
+    // exactly the (k+1)-th largest G
+    unsigned long long lo = 0;
+    while (ce == cudaSuccess && lo < hi) {
+        const unsigned long long mid = lo + (hi - lo + 1) / 2;
+        unsigned int c = 0;
+        ce = cudaMemsetAsync(cnt, 0, sizeof c, st);
+        if (ce != cudaSuccess) break;
+        launch_count_ge(h->T, h->G, mid, cnt, st);
+        ce = cudaMemcpyAsync(&c, cnt, sizeof c, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) break;
+        if (c >= (unsigned int)k + 1u) lo = mid;
+        else hi = mid - 1;
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(sel, &lo, sizeof lo, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return done(fail(RDSPLIT_ECUDA, "%s: %s", where, cudaGetErrorString(ce)));
+    }
+    launch_tau(h->D, h->S, sel, h->tau_scale, h->d_tau, st);
+    ce = cudaMemcpyAsync(&h->tau, h->d_tau, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return done(fail(RDSPLIT_ECUDA, "%s: %s", where, cudaGetErrorString(ce)));
+    }
+    if (std::isfinite(h->tau)) launch_thresholds(h->T, h->mp, h->g, h->G, h->tau, h->thr, st);
+    if ((rc = launch_check(where))) return done(rc);
+    h->outliers = k;
+    return done(check_err(h, where));
+}
+
+int rdsplit_zeta_histogram(rdsplit_mesh_t h, int32_t nbins, int64_t* counts, double* mean, double* max_zeta) {
+    const char* where = "rdsplit_zeta_histogram";
+    if (!h || !counts) return fail(RDSPLIT_EINVAL, "%s: NULL argument", where);
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "%s: no model attached", where);
+    if (nbins < 1 || nbins > (1 << 20)) return fail(RDSPLIT_EINVAL, "%s: nbins must be in 1..2^20", where);
+    double dmax = 0.0;
+    for (int s = 0; s < h->S; ++s) dmax = std::max(dmax, h->mp.D[s]);
+    const double tau = std::isfinite(h->tau) ? h->tau : 0.0;
+    cudaStream_t st = h->stream;
+    unsigned long long* d_counts = nullptr;
+    double* d_sum = nullptr;
+    unsigned long long* d_max = nullptr;
+    int rc;
+    if ((rc = alloc_into(&d_counts, (size_t)nbins, "histogram")) || (rc = alloc_into(&d_sum, 1, "sum")) ||
+        (rc = alloc_into(&d_max, 1, "max"))) {
+        dev_free(d_counts);
+        dev_free(d_sum);
+        dev_free(d_max);
+        return rc;
+    }
+    std::vector<unsigned long long> hc((size_t)nbins);
+    double sum = 0.0;
+    unsigned long long mb = 0;
+    cudaError_t ce = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * nbins, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d_sum, 0, sizeof(double), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), st);
+    if (ce == cudaSuccess) {
+        launch_zeta_hist(h->T, h->G, tau, dmax, nbins, d_counts, d_sum, d_max, st);
+        ce = cudaMemcpyAsync(hc.data(), d_counts, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost, st);
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&sum, d_sum, sizeof sum, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&mb, d_max, sizeof mb, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    dev_free(d_counts);
+    dev_free(d_sum);
+    dev_free(d_max);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RDSPLIT_ECUDA, "%s: %s", where, cudaGetErrorString(ce));
+    }
+    if ((rc = launch_check(where))) return rc;
+    for (int b = 0; b < nbins; ++b) counts[b] = (int64_t)hc[b];
+    if (mean) *mean = sum / (double)h->T;
+    if (max_zeta) std::memcpy(max_zeta, &mb, sizeof(double));
+    return RDSPLIT_OK;
+}
+
 int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, const int32_t* lhs,
                       const int32_t* rhs, const double* k, const uint8_t* mask, double tau_scale) {
     if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_model: NULL handle");
@@ -333,6 +436,8 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
     h->mp = mp;
     h->S = S;
     h->R = R;
+    h->tau_scale = tau_scale;
+    h->outliers = 0;
     h->has_model = true;
     h->t = 0.0;
     h->period = 0;

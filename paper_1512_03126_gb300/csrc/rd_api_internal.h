@@ -41,6 +41,8 @@ struct rdsplit_mesh {
     rdk::ModelParams mp{};
     bool has_model = false;
     int32_t rule = 0;          // transfer rule, kept across rdsplit_set_model
+    double tau_scale = 1.0;    // of the attached model
+    int32_t outliers = 0;      // fastest tets left out of the choice of tau
     // sampled kernel timing
     int32_t timing_stride = 0;
     std::vector<cudaEvent_t> ev_pool;

@@ -77,6 +77,9 @@ void launch_tau(const double* D, int32_t S, const unsigned long long* gmax_bits,
 void launch_thresholds(int32_t T, const ModelParams& mp, const double* g, const double* G, double tau_k,
                        uint4* thr, cudaStream_t st);
 void launch_avv(int32_t T, const double* vol, float2* avv, cudaStream_t st);
+void launch_count_ge(int32_t T, const double* G, unsigned long long xbits, unsigned int* count, cudaStream_t st);
+void launch_zeta_hist(int32_t T, const double* G, double tau, double D, int32_t nbins, unsigned long long* counts,
+                      double* sum, unsigned long long* maxbits, cudaStream_t st);
 void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, cudaStream_t st);
 void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* st_major, uint32_t* err,
                       cudaStream_t st);

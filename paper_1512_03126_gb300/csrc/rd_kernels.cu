@@ -5,6 +5,8 @@
 //                  table, mesh validation, max G           (setup, Sec. II.A)
 //   k_tau          tau = tau_scale / max_s(D_s * max_t G_t) (Algorithm 1, precompute)
 //   k_thresholds   cumulative 32-bit face thresholds of zeta * w_f
+//   k_count_ge     tets with G >= x (rank selection for the outlier option)
+//   k_zeta_hist    histogram of zeta over the tets (diagnostic, Fig. 1d)
 //   k_period       per tet: gather of the previous period's transfers, SSA
 //                  reactions with occupancy (Step 2), mean-corrected binomial
 //                  count and multinomial split (Step 3)
@@ -13,6 +15,7 @@
 // Layout: counts and remainders are species-major int32 [S][T] (coalesced);
 // out-slots are int4 [S][T] (one 16-byte store per tet and species, the four
 // faces of a tet in one sector so that neighbours reading them share it).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -97,6 +100,44 @@ __global__ void k_tau(const double* D, int32_t S, const unsigned long long* gmax
 void launch_tau(const double* D, int32_t S, const unsigned long long* gmax_bits, double tau_scale,
                 double* tau_out, cudaStream_t st) {
     k_tau<<<1, 32, 0, st>>>(D, S, gmax_bits, tau_scale, tau_out);
+    ++g_launches;
+}
+
+// Number of tets with G_t >= x (x given by its bit pattern; G >= 0, so bit
+// order is value order): one step of the rank selection behind the outlier
+// option of Sec. II.A.
+__global__ void k_count_ge(int32_t T, const double* __restrict__ G, unsigned long long xbits, unsigned int* count) {
+    unsigned int c = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+        c += (unsigned long long)__double_as_longlong(G[t]) >= xbits ? 1u : 0u;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+void launch_count_ge(int32_t T, const double* G, unsigned long long xbits, unsigned int* count, cudaStream_t st) {
+    k_count_ge<<<std::min(grid_for(T), 1024), kBlock, 0, st>>>(T, G, xbits, count);
+    ++g_launches;
+}
+
+// Histogram of zeta_t = min(1, tau * (D * G_t)) over the tets (Fig. 1d: the
+// fastest species' zeta), bins of width 1/nbins on [0, 1] with zeta = 1 in the
+// last; also the sum and the largest value (as bits; zeta >= 0).
+__global__ void k_zeta_hist(int32_t T, const double* __restrict__ G, double tau, double D, int32_t nbins,
+                            unsigned long long* counts, double* sum, unsigned long long* maxbits) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        double z = tau * (D * G[t]);
+        if (z > 1.0) z = 1.0;
+        int b = (int)(z * (double)nbins);
+        if (b >= nbins) b = nbins - 1;
+        atomicAdd(counts + b, 1ull);
+        atomicAdd(sum, z);
+        atomicMax(maxbits, (unsigned long long)__double_as_longlong(z));
+    }
+}
+
+void launch_zeta_hist(int32_t T, const double* G, double tau, double D, int32_t nbins, unsigned long long* counts,
+                      double* sum, unsigned long long* maxbits, cudaStream_t st) {
+    k_zeta_hist<<<std::min(grid_for(T), 1024), kBlock, 0, st>>>(T, G, tau, D, nbins, counts, sum, maxbits);
     ++g_launches;
 }
 

@@ -63,6 +63,8 @@ def _declare(L):
         "rdsplit_engine_destroy": ([vp], C.c_int),
         "rdsplit_ensemble_run": ([i32, vp, vp, vp], C.c_int),
         "rdsplit_engine_set_timing": ([vp, i32], C.c_int),
+        "rdsplit_set_zeta_outliers": ([vp, i32], C.c_int),
+        "rdsplit_zeta_histogram": ([vp, i32, vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
         "rdsplit_set_transfer_rule": ([vp, i32], C.c_int),
         "rdsplit_engine_set_concurrency": ([vp, i32, i32], C.c_int),
         "rdsplit_engine_set_bitmap_smem": ([vp, i32], C.c_int),
@@ -256,6 +258,18 @@ def rdsplit_engine_destroy(e):
 RDSPLIT_TRANSFER_MEAN = 0   # N-bar, the mean occupancy (Eq. 3): the method
 RDSPLIT_TRANSFER_END = 1    # N(tau_k): first-order splitting
 RDSPLIT_TRANSFER_MID = 2    # N(tau_k / 2): the half-step reading
+
+
+def rdsplit_set_zeta_outliers(h, k: int):
+    _check(lib().rdsplit_set_zeta_outliers(h, int(k)))
+
+
+def rdsplit_zeta_histogram(h, nbins: int):
+    """Returns (counts int64[nbins], mean, max) of zeta over the tets."""
+    counts = np.zeros(int(nbins), np.int64)
+    mean, mx = C.c_double(), C.c_double()
+    _check(lib().rdsplit_zeta_histogram(h, int(nbins), _ptr(counts), C.byref(mean), C.byref(mx)))
+    return counts, mean.value, mx.value
 
 
 def rdsplit_set_transfer_rule(h, rule: int):

@@ -249,3 +249,47 @@ def test_full_size_against_stored_oracle_runs(rd, name):
     assert p == rec["period"]
     assert [int(x) for x in g.sum(0)] == rec["totals"]
     assert hashlib.sha256(np.ascontiguousarray(g, dtype="<i4").tobytes()).hexdigest() == rec["sha256"]
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_zeta_outliers_bit_exact(rd, oracle, k):
+    """The outlier option (Sec. II.A): tau from the (k+1)-th fastest tet,
+    equal to the oracle's, and the run equals the oracle's with the same
+    option, dense and batched."""
+    m = I.cube(5, 1e-6, 0.2, 12)
+    n = I.molecules(20e-6, 1e-18)
+    w = I.Workload("abc_n5", m, I.abc_model(), I.place_by_volume(m, [n, n, n // 3], 4), 2e-3, 7)
+    ref, t_ref, p_ref = oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed, outliers=k)
+    with rd.Simulation(w.mesh, w.model, w.counts) as sim:
+        base_tau = sim.tau
+        rd.rdsplit_set_zeta_outliers(sim.h, k)
+        assert sim.tau == oracle.tau(w.mesh, w.model, outliers=k) > base_tau
+        sim.run(w.t_end, w.seed)
+        assert_same(sim.counts(), ref)
+        assert sim.time == (t_ref, p_ref)
+    with rd.Simulation(w.mesh, w.model, w.counts) as sim:
+        rd.rdsplit_set_zeta_outliers(sim.h, k)
+        rd.rdsplit_ensemble_run([sim.h], [w.t_end], [w.seed])
+        assert_same(sim.counts(), ref)
+
+
+def test_zeta_histogram(rd):
+    """Fig. 1d diagnostic: the histogram of zeta over the tets matches the
+    same quantity computed on the host from the mesh, and the outlier option
+    moves k tets to zeta = 1."""
+    m = I.cube(6, 1e-6, 0.2, 5)
+    model = I.diffusion_model(1e-12)
+    inner = m.adj >= 0
+    g = np.where(inner, m.area / (m.vol[:, None] * np.where(inner, m.dist, 1.0)), 0.0)
+    G = ((g[:, 0] + g[:, 1]) + g[:, 2]) + g[:, 3]
+    with rd.Simulation(m, model) as sim:
+        for k in (0, 6):
+            if k:
+                rd.rdsplit_set_zeta_outliers(sim.h, k)
+            z = np.minimum(1.0, sim.tau * (1e-12 * G))
+            counts, mean, mx = rd.rdsplit_zeta_histogram(sim.h, 20)
+            ref = np.bincount(np.minimum((z * 20).astype(int), 19), minlength=20)
+            assert counts.sum() == m.n_tets
+            assert np.abs(counts - ref).max() <= 1
+            assert abs(mean - z.mean()) < 1e-12 and abs(mx - z.max()) <= 1e-15
+            assert (z >= 1.0).sum() >= k and counts[-1] >= k
