@@ -50,6 +50,10 @@ def lib():
         L.orc_run_opts.restype = C.c_int
         L.orc_tau_outliers.argtypes = L.orc_tau.argtypes + [C.c_int32]
         L.orc_tau_outliers.restype = C.c_double
+        L.orc_run_foil.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_double,
+                                   _i32p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_double, C.c_uint64,
+                                   C.c_int64, C.c_int32]
+        L.orc_run_foil.restype = C.c_int
         L.orc_issa_run.argtypes = [C.c_int32, _i32p, _f64p, _f64p, _f64p, C.c_int32, _f64p, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _i32p, C.c_double,
                                    C.c_uint64]
@@ -170,6 +174,28 @@ def run(mesh, model, counts, t_end: float, seed: int, t0: float = 0.0, period0: 
                             int(seed), int(max_periods), int(rule), int(outliers))
     if rc != 0:
         raise OracleError(f"orc_run_opts failed with code {rc}")
+    return c, t.value, p.value
+
+
+# Validation foils (Sec. II.A, Fig. 2), test-only diffusion counts.
+FOIL_MEAN_N = 1   # n = discrete mean of the gross transfer (Fig. 2(b))
+FOIL_NET = 2      # transfer binomial on the net flux only (Fig. 2(c))
+
+
+def run_foil(mesh, model, counts, t_end: float, seed: int, foil: int, t0: float = 0.0, period0: int = 0,
+             max_periods: int = -1):
+    """Pure diffusion with a validation foil in place of the binomial count.
+    Returns (counts [T][S] int32, t, period)."""
+    S, R, D, *_ = _model_arrays(model)
+    assert R == 0, "the foils are defined for pure diffusion"
+    c = np.ascontiguousarray(counts, np.int32).copy()
+    assert c.shape == (mesh.n_tets, S)
+    t = C.c_double(t0)
+    p = C.c_int64(period0)
+    rc = lib().orc_run_foil(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, S, D, float(model.tau_scale),
+                            c, C.byref(t), C.byref(p), float(t_end), int(seed), int(max_periods), int(foil))
+    if rc != 0:
+        raise OracleError(f"orc_run_foil failed with code {rc}")
     return c, t.value, p.value
 
 

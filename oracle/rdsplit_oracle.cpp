@@ -434,6 +434,25 @@ void react_tet(const Problem& P, int t, uint32_t period, double tau_k, uint64_t 
 //  left.  The paper switches at n = 10 for speed on a CPU; this build
 //  switches at 4096, where one draw per molecule spread over a warp is
 //  faster on the GPU than the double-precision samplers.
+// Step 3.3: n molecules split over the faces multinomially by conditional
+// binomials in canonical face order, p_i = g_i / (g_i + ... + g_3), the last
+// face with a neighbour taking the rest.
+void split_over_faces(const double* g, int64_t n, Stream& st, int64_t out[4]) {
+    double suf[4];
+    double acc = 0.0;
+    for (int f = 3; f >= 0; --f) { acc = g[f] + acc; suf[f] = acc; }
+    int last = -1;
+    for (int f = 0; f < 4; ++f) if (g[f] > 0.0) last = f;
+    int64_t m = n;
+    for (int f = 0; f < 4; ++f) {
+        if (!(g[f] > 0.0)) continue;
+        if (f == last) { out[f] = m; break; }
+        int64_t nf = binomial(m, g[f] / suf[f], st);
+        out[f] = nf;
+        m -= nf;
+    }
+}
+
 void diffuse_tet_species(const Problem& P, const Geometry& geo, int t, int s, uint32_t period,
                          double tau_k, uint64_t seed, int64_t Nt, bool touched, double occ,
                          int64_t Nmid, int64_t out[4]) {
@@ -474,18 +493,59 @@ void diffuse_tet_species(const Problem& P, const Geometry& geo, int t, int s, ui
     int64_t n = binomial(Nstar, zeta, st);
     if (n > Nt) n = Nt;
     if (n == 0) return;
-    double suf[4];
-    double acc = 0.0;
-    for (int f = 3; f >= 0; --f) { acc = g[f] + acc; suf[f] = acc; }
-    int last = -1;
-    for (int f = 0; f < 4; ++f) if (g[f] > 0.0) last = f;
-    int64_t m = n;
+    split_over_faces(g, n, st, out);
+}
+
+// Validation foils (Sec. II.A, Fig. 2(b, c)): diffusion counts the paper
+// shows to lose spatial noise.  Test-only; pure diffusion.
+//  kFoilMeanN  n is the discrete mean of the gross transfer, floor(zeta N +
+//              1/2), split over the faces multinomially (Fig. 2(b)).
+//  kFoilNet    molecules move only with the net flux: through face f to u,
+//              the expected gross flows are zeta_t w_tf N_t out and
+//              zeta_u w_ur N_u in (r the reverse face); the number sent is
+//              binomial with probability max(0, out - in) / N_t per molecule,
+//              the faces drawn by conditional binomials (Fig. 2(c), "binomial
+//              but based on net diffusive flux").
+const int kFoilMeanN = 1;
+const int kFoilNet = 2;
+
+void diffuse_foil(const Problem& P, const Geometry& geo, const std::vector<int32_t>& rev,
+                  const std::vector<int64_t>& N, int foil, int t, int s, uint32_t period, double tau_k,
+                  uint64_t seed, int64_t Nt, int64_t out[4]) {
+    out[0] = out[1] = out[2] = out[3] = 0;
+    const double Gt = geo.G[t];
+    const double zeta = zeta_of(tau_k, P.D[s], Gt);
+    if (!(zeta > 0.0) || Nt <= 0) return;
+    const double* g = &geo.g[4 * t];
+    Stream st(seed, (uint32_t)t, period, kDiffusion, (uint32_t)s);
+    if (foil == kFoilMeanN) {
+        int64_t n = (int64_t)std::floor(zeta * (double)Nt + 0.5);
+        if (n > Nt) n = Nt;
+        if (n > 0) split_over_faces(g, n, st, out);
+        return;
+    }
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
     for (int f = 0; f < 4; ++f) {
-        if (!(g[f] > 0.0)) continue;
-        if (f == last) { out[f] = m; break; }
-        int64_t nf = binomial(m, g[f] / suf[f], st);
-        out[f] = nf;
-        m -= nf;
+        const int u = P.adj[4 * t + f];
+        if (u < 0) continue;
+        const double flow_out = zeta * (g[f] / Gt) * (double)Nt;
+        const double Gu = geo.G[u];
+        const double zu = zeta_of(tau_k, P.D[s], Gu);
+        const double flow_in = zu * (geo.g[4 * u + rev[4 * t + f]] / Gu) * (double)N[(size_t)u * P.S + s];
+        const double net = flow_out - flow_in;
+        p[f] = net > 0.0 ? net / (double)Nt : 0.0;
+    }
+    int64_t rest = Nt;
+    double q = 1.0;
+    for (int f = 0; f < 4 && rest > 0; ++f) {
+        if (!(p[f] > 0.0)) continue;
+        double pf = p[f] / q;
+        if (pf > 1.0) pf = 1.0;
+        const int64_t x = binomial(rest, pf, st);
+        out[f] = x;
+        rest -= x;
+        q = q - p[f];
+        if (!(q > 0.0)) break;
     }
 }
 
@@ -622,6 +682,63 @@ int orc_run_opts(int32_t T, const int32_t* adj, const double* vol, const double*
             }
         }
         // Step 4.
+        t_now = last ? t_end : t_now + geo.tau;
+        period += 1;
+        done += 1;
+    }
+    for (size_t i = 0; i < N.size(); ++i) counts[i] = (int32_t)N[i];
+    *t_io = t_now;
+    *period_io = period;
+    return 0;
+}
+
+// Pure diffusion with a validation foil in place of the binomial count
+// (kFoilMeanN or kFoilNet; test-only, Fig. 2).  Same arguments and returns
+// as orc_run without reactions.
+int orc_run_foil(int32_t T, const int32_t* adj, const double* vol, const double* area, const double* dist,
+                 int32_t S, const double* D, double tau_scale, int32_t* counts, double* t_io, int64_t* period_io,
+                 double t_end, uint64_t seed, int64_t max_periods, int32_t foil) {
+    if (T <= 0 || S <= 0 || S > kMaxSpecies) return -1;
+    if (foil != kFoilMeanN && foil != kFoilNet) return -1;
+    Problem P{T, S, 0, adj, vol, area, dist, D, nullptr, nullptr, nullptr, nullptr, tau_scale, kRuleMean, 0};
+    Geometry geo = setup_geometry(P);
+    std::vector<int64_t> N((size_t)T * S), rem((size_t)T * S), out((size_t)T * S * 4);
+    for (size_t i = 0; i < N.size(); ++i) N[i] = counts[i];
+    std::vector<int32_t> rev((size_t)T * 4, -1);
+    for (int t = 0; t < T; ++t)
+        for (int f = 0; f < 4; ++f) {
+            int u = adj[4 * t + f];
+            if (u < 0) continue;
+            for (int r = 0; r < 4; ++r) if (adj[4 * u + r] == t) rev[4 * t + f] = r;
+            if (rev[4 * t + f] < 0) return -1;
+        }
+    double t_now = *t_io;
+    int64_t period = *period_io;
+    int64_t done = 0;
+    while (t_now < t_end && (max_periods < 0 || done < max_periods)) {
+        double tau_k = geo.tau;
+        bool last = false;
+        if (t_now + geo.tau > t_end) { tau_k = t_end - t_now; last = true; }
+        for (int t = 0; t < T; ++t)
+            for (int s = 0; s < S; ++s) {
+                int64_t o[4];
+                const int64_t Nt = N[(size_t)t * S + s];
+                diffuse_foil(P, geo, rev, N, foil, t, s, (uint32_t)period, tau_k, seed, Nt, o);
+                int64_t sum = 0;
+                for (int f = 0; f < 4; ++f) { out[((size_t)t * S + s) * 4 + f] = o[f]; sum += o[f]; }
+                rem[(size_t)t * S + s] = Nt - sum;
+            }
+        for (int t = 0; t < T; ++t)
+            for (int s = 0; s < S; ++s) {
+                int64_t v = rem[(size_t)t * S + s];
+                for (int f = 0; f < 4; ++f) {
+                    int u = adj[4 * t + f];
+                    if (u >= 0) v += out[((size_t)u * S + s) * 4 + rev[4 * t + f]];
+                }
+                if (v < 0) return -2;
+                if (v > 2147483647) return -3;
+                N[(size_t)t * S + s] = v;
+            }
         t_now = last ? t_end : t_now + geo.tau;
         period += 1;
         done += 1;
