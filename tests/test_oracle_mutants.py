@@ -48,7 +48,7 @@ MUTANTS = {
         [lambda o: L.test_comparison_rules_exact_laws(o, 1)]),
     "split_without_renormalisation": (
         "int64_t nf = binomial(m, g[f] / suf[f], st);",
-        "int64_t nf = binomial(m, g[f] / geo.G[t], st);",
+        "int64_t nf = binomial(m, g[f] / suf[0], st);",
         [lambda o: L.test_exact_law_of_pure_diffusion(o, 6000)]),
     "thresholds_not_cumulative": (
         "C[f] = threshold_of(zeta * (cum / Gt));",
