@@ -549,6 +549,25 @@ void diffuse_foil(const Problem& P, const Geometry& geo, const std::vector<int32
     }
 }
 
+// The synchronous transfer (Sec. III.D: changes buffered, then applied):
+// N'[t] = rem[t] + sum over faces of what the neighbour sent through the
+// shared face.  Returns 0, -2 for a negative count, -3 above 2^31 - 1.
+int apply_transfers(int T, int S, const int32_t* adj, const std::vector<int32_t>& rev,
+                    const std::vector<int64_t>& rem, const std::vector<int64_t>& out, std::vector<int64_t>& N) {
+    for (int t = 0; t < T; ++t)
+        for (int s = 0; s < S; ++s) {
+            int64_t v = rem[(size_t)t * S + s];
+            for (int f = 0; f < 4; ++f) {
+                int u = adj[4 * t + f];
+                if (u >= 0) v += out[((size_t)u * S + s) * 4 + rev[4 * t + f]];
+            }
+            if (v < 0) return -2;
+            if (v > 2147483647) return -3;
+            N[(size_t)t * S + s] = v;
+        }
+    return 0;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C API ---
@@ -663,17 +682,7 @@ int orc_run_opts(int32_t T, const int32_t* adj, const double* vol, const double*
         }
         // Synchronous transfer: every tet keeps what did not leave and
         // receives what its neighbours sent through the shared faces.
-        for (int t = 0; t < T; ++t)
-            for (int s = 0; s < S; ++s) {
-                int64_t v = rem[(size_t)t * S + s];
-                for (int f = 0; f < 4; ++f) {
-                    int u = adj[4 * t + f];
-                    if (u >= 0) v += out[((size_t)u * S + s) * 4 + rev[4 * t + f]];
-                }
-                if (v < 0) return -2;
-                if (v > 2147483647) return -3;
-                N[(size_t)t * S + s] = v;
-            }
+        if (int rc = apply_transfers(T, S, adj, rev, rem, out, N)) return rc;
         if (R == 0) {
             for (int s = 0; s < S; ++s) {
                 int64_t tot = 0;
@@ -728,17 +737,7 @@ int orc_run_foil(int32_t T, const int32_t* adj, const double* vol, const double*
                 for (int f = 0; f < 4; ++f) { out[((size_t)t * S + s) * 4 + f] = o[f]; sum += o[f]; }
                 rem[(size_t)t * S + s] = Nt - sum;
             }
-        for (int t = 0; t < T; ++t)
-            for (int s = 0; s < S; ++s) {
-                int64_t v = rem[(size_t)t * S + s];
-                for (int f = 0; f < 4; ++f) {
-                    int u = adj[4 * t + f];
-                    if (u >= 0) v += out[((size_t)u * S + s) * 4 + rev[4 * t + f]];
-                }
-                if (v < 0) return -2;
-                if (v > 2147483647) return -3;
-                N[(size_t)t * S + s] = v;
-            }
+        if (int rc = apply_transfers(T, S, adj, rev, rem, out, N)) return rc;
         t_now = last ? t_end : t_now + geo.tau;
         period += 1;
         done += 1;
