@@ -386,7 +386,9 @@ def run_ensemble(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("k_engine_run", "ensemble"),
                 "bytes_per_entry": bpe, "entries_per_launch": round(entries / launches_per_step, 1),
                 "launch_us": round(per_launch_s * 1e6, 3), "sampled_launches": kn,
-                "peak_source": f"{peak_kind} hbm_gbs"}
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "limit": "not HBM: DRAM moves ~2 B per entry (L2 serves the active tets); instruction issue at "
+                         "16 warps/SM and the per-period cluster barrier bound it (profiles/k_engine_run_ensemble.md)"}
 
     # the plain form: each simulation through its own rdsplit_run
     plain = None
