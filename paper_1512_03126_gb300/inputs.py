@@ -200,6 +200,82 @@ def kuhn_box(nx: int, ny: int, nz: int, size=(1e-6, 1e-6, 1e-6),
                 size=(Lx, Ly, Lz))
 
 
+def triangle_sheet(nx: int, ny: int, size=(1e-6, 1e-6), jitter: float = 0.0, mesh_seed: int = 0) -> Mesh:
+    """Flat triangulated rectangle for surface diffusion (Sec. III.A:
+    transfer between surface triangles): ``nx*ny`` cells, each split into two
+    triangles along the diagonal from its lower-left corner; interior vertices
+    jittered by up to ``jitter`` of the spacing (seeded), halved where a
+    triangle would fall below 5% of its unjittered area.
+
+    Returned in the arrays of the C ABI, read for a surface: ``vol`` is the
+    triangle area (m^2), ``area[t][f]`` the length of the edge opposite local
+    vertex ``f`` (m), ``dist`` the distance between triangle centroids, and
+    the fourth neighbour slot is -1.  The face coefficient A/(V dist) is then
+    L/(A dist) (1/m^2) and D times its sum the triangle's hop rate (1/s),
+    the two-dimensional form of the same rate.
+    """
+    Lx, Ly = size
+    hx, hy = Lx / nx, Ly / ny
+    gx, gy = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    gx, gy = gx.reshape(-1), gy.reshape(-1)
+    X0 = np.stack([gx * hx, gy * hy], axis=1).astype(np.float64)
+    vid = lambda i, j: j * (nx + 1) + i
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            tris.append((vid(i, j), vid(i + 1, j), vid(i + 1, j + 1)))
+            tris.append((vid(i, j), vid(i + 1, j + 1), vid(i, j + 1)))
+    tri = np.array(tris, np.int64)
+    interior = (gx > 0) & (gx < nx) & (gy > 0) & (gy < ny)
+    d = np.zeros_like(X0)
+    if jitter > 0.0:
+        rng = np.random.Generator(np.random.PCG64(mesh_seed))
+        d = rng.uniform(-jitter, jitter, size=X0.shape) * np.array([hx, hy])
+        d[~interior] = 0.0
+
+    def signed_areas(X):
+        P = X[tri]
+        e1, e2 = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+        return 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]), P
+
+    X = X0 + d
+    sa, P = signed_areas(X)
+    for _ in range(60):
+        bad = sa < 0.05 * 0.5 * hx * hy
+        if not bad.any():
+            break
+        vb = np.unique(tri[bad].reshape(-1))
+        d[vb] *= 0.5
+        X = X0 + d
+        sa, P = signed_areas(X)
+    if np.any(sa <= 0):
+        raise ValueError("inverted triangle in the mesh")
+    T = tri.shape[0]
+    # neighbours across the edge opposite each local vertex
+    edge_owner = {}
+    adj = -np.ones((T, 4), np.int32)
+    for t in range(T):
+        for f in range(3):
+            a, b = sorted((int(tri[t, (f + 1) % 3]), int(tri[t, (f + 2) % 3])))
+            if (a, b) in edge_owner:
+                u, g = edge_owner.pop((a, b))
+                adj[t, f], adj[u, g] = u, t
+            else:
+                edge_owner[(a, b)] = (t, f)
+    area = np.zeros((T, 4))
+    for f in range(3):
+        e = P[:, (f + 2) % 3] - P[:, (f + 1) % 3]
+        area[:, f] = np.sqrt(np.einsum("ij,ij->i", e, e))
+    cen2 = P.mean(axis=1)
+    cen = np.concatenate([cen2, np.zeros((T, 1))], axis=1)
+    nbc = cen[np.maximum(adj, 0)]
+    dv = nbc - cen[:, None, :]
+    dist = np.sqrt(np.einsum("ijk,ijk->ij", dv, dv))
+    dist[adj < 0] = 0.0
+    return Mesh(adj=adj, vol=np.ascontiguousarray(sa), area=np.ascontiguousarray(area),
+                dist=np.ascontiguousarray(dist), centroid=cen, shape=(nx, ny, 1), size=(Lx, Ly, 0.0))
+
+
 def cube(n: int, L: float = 1e-6, jitter: float = 0.0, mesh_seed: int = 0) -> Mesh:
     return kuhn_box(n, n, n, (L, L, L), jitter, mesh_seed)
 
