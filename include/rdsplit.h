@@ -8,7 +8,11 @@
  * tetrahedron runs its own SSA reactions (Sec. II.C, Step 2), then each
  * species sends n = Binomial(N-bar, zeta) molecules (Eq. 3) to its face
  * neighbours multinomially (Sec. II.B), and the transfers are applied
- * synchronously.
+ * synchronously.  Options: the paper's comparison transfer rules (Sec. II.C,
+ * rdsplit_set_transfer_rule) and its outlier choice of tau (Sec. II.A,
+ * rdsplit_set_zeta_outliers).  A triangle mesh passed with triangle areas as
+ * volumes, edge lengths as face areas and the fourth neighbour -1 gives
+ * surface diffusion (Sec. III.A).
  *
  * Conventions for every call:
  *   - Return value: 0 on success, else a negative RDSPLIT_E* code; the text
