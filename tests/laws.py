@@ -161,3 +161,21 @@ def influx_split_mean(mesh, D: float, a: np.ndarray, tau: float, periods: int, c
         out = zeta * (m + c * a * tau)
         m = m + a * tau - out + W @ out
     return m
+
+
+def production_dimer_decay(lam: float, c2: float, n0: int, t: float, n_max: int) -> np.ndarray:
+    """Law of A(t) for 0 -> A (rate lam) and 2A -> 0 (rate c2 per unordered
+    pair, so c2 * n (n - 1) / 2 in total) in one well-mixed volume, from
+    A(0) = n0, on states 0..n_max (n_max well above where the law has mass):
+    the chemical master equation solved by a matrix exponential."""
+    n = n_max + 1
+    Q = np.zeros((n, n))
+    for a in range(n):
+        if a + 1 < n:
+            Q[a, a + 1] = lam
+        if a >= 2:
+            Q[a, a - 2] = c2 * a * (a - 1) / 2.0
+        Q[a, a] = -(Q[a].sum())
+    p0 = np.zeros(n)
+    p0[n0] = 1.0
+    return p0 @ expm(Q * t)

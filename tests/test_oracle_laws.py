@@ -10,7 +10,7 @@ from scipy.stats import binom
 
 from paper_1512_03126_gb300 import inputs as I
 from tests.laws import (binomial_of_shifted_poisson, birth_death_ABC, chi2_pvalue, one_period_matrix,
-                        one_tet_mesh, two_tet_mesh)
+                        one_tet_mesh, production_dimer_decay, two_tet_mesh)
 
 
 def _src(counts):
@@ -126,6 +126,29 @@ def test_reversible_binding_matches_master_equation(oracle, two_tets):
     C = np.array([oracle.run(mesh, model, c0, t_end, s)[0][0, 2] for s in range(4000)])
     law = birth_death_ABC(8, 6, 0.5, 2.0, 0, t_end)
     assert chi2_pvalue(np.bincount(C, minlength=law.size), law) > 1e-4
+
+
+def production_dimer_model(vol: float, lam: float, c2: float, D: float = 0.0):
+    """0 -> A at lam molecules/s in a tet of volume vol, and 2A -> 0 at c2
+    per pair (the 'production and second-order degradation' model of
+    Sec. III.B, Fig. 6), in SI rate constants."""
+    nav = 6.02214076e23 * vol * 1e3
+    return I.Model(D=np.array([D]), lhs=np.array([[0], [2]], np.int32), rhs=np.array([[1], [0]], np.int32),
+                   k=np.array([lam / nav, c2 * nav]))
+
+
+def test_production_and_dimer_decay_matches_master_equation(oracle):
+    """Fig. 6's model in one tet: 0 -> A and 2A -> 0.  The law of A(t) is
+    the master equation's, which pins the propensity of a reaction with a
+    doubled reactant, c N (N - 1) / 2."""
+    vol = 1e-19
+    lam, c2, t_end = 40.0, 3.0, 0.4
+    mesh = one_tet_mesh(vol)
+    model = production_dimer_model(vol, lam, c2)
+    A = np.array([oracle.run(mesh, model, np.array([[3]], np.int32), t_end, s)[0][0, 0] for s in range(4000)])
+    law = production_dimer_decay(lam, c2, 3, t_end, 60)
+    assert law[-5:].sum() < 1e-12
+    assert chi2_pvalue(np.bincount(A, minlength=law.size), law) > 1e-4
 
 
 def test_mean_corrected_transfer(oracle):

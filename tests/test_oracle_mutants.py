@@ -30,6 +30,10 @@ MUTANTS = {
         "    } else if (P.rule == kRuleMean && touched) {\n        Stream rs(",
         "    } else if (false) {\n        Stream rs(",
         [L.test_mean_corrected_transfer]),
+    "dimer_counts_ordered_pairs": (
+        "else if (nu == 2) h = h * (N[s] * (N[s] - 1) / 2);",
+        "else if (nu == 2) h = h * (N[s] * N[s] / 2);",
+        [L.test_production_and_dimer_decay_matches_master_equation]),
     "outlier_rank_off_by_one": (
         "    const double dsel = dt[P.outliers];",
         "    const double dsel = dt[P.outliers > 0 ? P.outliers - 1 : 0];",
