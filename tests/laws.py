@@ -179,3 +179,41 @@ def production_dimer_decay(lam: float, c2: float, n0: int, t: float, n_max: int)
     p0 = np.zeros(n)
     p0[n0] = 1.0
     return p0 @ expm(Q * t)
+
+
+def irwin_hall_density_at_integer(n: int, x: int) -> float:
+    """Density of the sum of n independent Uniform(0, 1) at the integer x,
+    f_n(x) = sum_{k <= x} (-1)^k C(n, k) (x - k)^(n-1) / (n-1)!, evaluated in
+    exact integer arithmetic (the alternating sum cancels badly in floats)."""
+    if n < 1 or x <= 0 or x >= n:
+        return 0.0
+    num = sum((-1) ** k * math.comb(n, k) * (x - k) ** (n - 1) for k in range(0, x + 1))
+    return num / math.factorial(n - 1)
+
+
+def mean_rule_influx_law(n0: int, lam: float, zeta: float, kmax: int) -> np.ndarray:
+    """Exact law of the count sent in one period under the mean-occupancy
+    rule (Eq. 3 with unbiased stochastic rounding), for a tet holding n0 with
+    a Poisson influx of mean lam over the period and one neighbour (all of
+    zeta towards it), nothing else reacting.  Given m arrivals at uniform
+    times, N-bar = n0 + S with S a sum of m uniforms; rounding gives
+    N* = n0 + j with probability E[max(0, 1 - |S - j|)], which is the
+    Irwin-Hall(m + 2) density at j + 1 (S plus the difference of two
+    uniforms); then n ~ Binomial(N*, zeta)."""
+    out = np.zeros(kmax + 1)
+    mmax = int(lam + 12 * math.sqrt(lam) + 30)
+    for m in range(mmax + 1):
+        wm = math.exp(-lam + m * math.log(lam) - math.lgamma(m + 1))
+        for j in range(0, m + 1):
+            pj = 1.0 if m == 0 and j == 0 else irwin_hall_density_at_integer(m + 2, j + 1)
+            if pj == 0.0:
+                continue
+            n = n0 + j
+            if zeta >= 1.0:                       # every counted molecule leaves
+                if n <= kmax:
+                    out[n] += wm * pj
+                continue
+            k = np.arange(0, min(n, kmax) + 1)
+            lg = np.array([math.lgamma(n + 1) - math.lgamma(i + 1) - math.lgamma(n - i + 1) for i in k])
+            out[: k.size] += wm * pj * np.exp(lg + k * math.log(zeta) + (n - k) * math.log1p(-zeta))
+    return out

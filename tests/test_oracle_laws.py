@@ -9,8 +9,8 @@ import pytest
 from scipy.stats import binom
 
 from paper_1512_03126_gb300 import inputs as I
-from tests.laws import (binomial_of_shifted_poisson, birth_death_ABC, chi2_pvalue, one_period_matrix,
-                        one_tet_mesh, production_dimer_decay, two_tet_mesh)
+from tests.laws import (binomial_of_shifted_poisson, birth_death_ABC, chi2_pvalue, mean_rule_influx_law,
+                        one_period_matrix, one_tet_mesh, production_dimer_decay, two_tet_mesh)
 
 
 def _src(counts):
@@ -221,6 +221,24 @@ def test_comparison_rules_exact_laws(oracle, rule):
         mean_rule = np.array([oracle.run(mesh, model, c0, np.inf, s, max_periods=1)[0][1, 0]
                               for s in range(20000)])
         assert chi2_pvalue(np.bincount(mean_rule, minlength=law.size), law) < 1e-6
+
+
+@pytest.mark.parametrize("n0, a_tau, zeta, seeds", [(5, 20.0, 0.5, 20000), (0, 2.0, 1.0, 40000)])
+def test_mean_rule_exact_law(oracle, n0, a_tau, zeta, seeds):
+    """The law, not only the mean, of the method's transfer (Eq. 3 with the
+    unbiased stochastic rounding of reading 4): with a Poisson influx the
+    occupancy mean is N0 plus a sum of uniforms, and the sent count has the
+    closed-form law of laws.mean_rule_influx_law (chi-square).  With zeta = 1
+    every counted molecule leaves, so the second case sees N* itself, where
+    a rounding to the nearest integer instead of the stochastic one shows."""
+    mesh, model, c0 = _influx_two_tets(a_tau, zeta)
+    c0[0, 0] = n0
+    n = np.array([oracle.run(mesh, model, c0, np.inf, s, max_periods=1)[0][1, 0] for s in range(seeds)])
+    law = mean_rule_influx_law(n0, a_tau, zeta, int(n.max()) + 20)
+    assert chi2_pvalue(np.bincount(n, minlength=law.size), law) > 1e-4
+    if zeta < 1.0:
+        other = binomial_of_shifted_poisson(n0, a_tau / 2, zeta, law.size - 1)
+        assert chi2_pvalue(np.bincount(n, minlength=law.size), other) < 1e-6
 
 
 def test_rules_agree_without_reactions(oracle):

@@ -30,6 +30,10 @@ MUTANTS = {
         "    } else if (P.rule == kRuleMean && touched) {\n        Stream rs(",
         "    } else if (false) {\n        Stream rs(",
         [L.test_mean_corrected_transfer]),
+    "rounding_to_nearest": (
+        "Nstar = (int64_t)fl + (rs.u01() < frac ? 1 : 0);",
+        "Nstar = (int64_t)fl + (frac >= 0.5 ? 1 : 0);",
+        [lambda o: L.test_mean_rule_exact_law(o, 0, 2.0, 1.0, 40000)]),
     "dimer_counts_ordered_pairs": (
         "else if (nu == 2) h = h * (N[s] * (N[s] - 1) / 2);",
         "else if (nu == 2) h = h * (N[s] * N[s] / 2);",
