@@ -241,6 +241,26 @@ def test_mean_rule_exact_law(oracle, n0, a_tau, zeta, seeds):
         assert chi2_pvalue(np.bincount(n, minlength=law.size), other) < 1e-6
 
 
+def test_transfer_is_capped_by_the_molecules_present(oracle):
+    """Reading 5: n = min(Binomial(N*, zeta), N(tau_k)).  Under a first-order
+    decay N-bar exceeds the survivors N(tau_k) (counts only fall), so with
+    zeta = 1 the cap binds: exactly the survivors leave.  The tet ends empty
+    and its neighbour holds Binomial(40, e^{-k tau}) molecules."""
+    vol = 1e-19
+    mesh = two_tet_mesh((vol, vol))
+    model0 = I.diffusion_model(1e-12)
+    model0.tau_scale = 1.0
+    tau = oracle.tau(mesh, model0)
+    k = 2.0 / tau
+    model = I.Model(D=np.array([1e-12]), lhs=np.ones((1, 1), np.int32), rhs=np.zeros((1, 1), np.int32),
+                    k=np.array([k]), tau_scale=1.0)
+    c0 = np.array([[40], [0]], np.int32)
+    got = np.array([oracle.run(mesh, model, c0, np.inf, s, max_periods=1)[0][:, 0] for s in range(3000)])
+    assert np.all(got[:, 0] == 0)
+    law = binom.pmf(np.arange(41), 40, math.exp(-2.0))
+    assert chi2_pvalue(np.bincount(got[:, 1], minlength=41), law) > 1e-4
+
+
 def test_rules_agree_without_reactions(oracle):
     """Without reactions N-bar = N(tau/2) = N(tau): the three rules give the
     same counts, draw for draw."""

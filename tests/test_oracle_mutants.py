@@ -34,6 +34,10 @@ MUTANTS = {
         "Nstar = (int64_t)fl + (rs.u01() < frac ? 1 : 0);",
         "Nstar = (int64_t)fl + (frac >= 0.5 ? 1 : 0);",
         [lambda o: L.test_mean_rule_exact_law(o, 0, 2.0, 1.0, 40000)]),
+    "no_cap_at_molecules_present": (
+        "            if (moved == Nt) break;",
+        "            if (false) break;",
+        [L.test_transfer_is_capped_by_the_molecules_present]),
     "dimer_counts_ordered_pairs": (
         "else if (nu == 2) h = h * (N[s] * (N[s] - 1) / 2);",
         "else if (nu == 2) h = h * (N[s] * N[s] / 2);",
