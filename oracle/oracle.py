@@ -7,7 +7,6 @@ samplers) and ``issa.cpp`` (exact spatial SSA).
 from __future__ import annotations
 
 import ctypes as C
-import math
 
 import numpy as np
 

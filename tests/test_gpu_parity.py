@@ -6,7 +6,6 @@ every count (tolerance 0).
 """
 import hashlib
 import json
-import math
 import os
 
 import numpy as np
