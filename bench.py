@@ -24,10 +24,8 @@ bounded sample on the host cores (``cpu_baseline``).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -41,18 +39,17 @@ import numpy as np  # noqa: E402
 
 METRIC = "tet-period updates/s"
 UNIT = "tet-period/s"
-PROFILES = os.path.join(ROOT, "profiles")
 
 
 # --------------------------------------------------------------- workloads --
 
 def engine_bytes_per_entry(S: int) -> int:
-    """Bytes the batched engine must move per processed (slot, tet) entry:
-    the reverse-face record (16), the next-period bitmap bit (one 4-byte
-    word update) and, per species, the count read and clear (8), the
-    thresholds (16), the kept-count add (4) and the four face adds (16).  The
-    bitmap scan (8 bytes per 32 tets and period) is not counted."""
-    return 20 + 44 * S
+    """Algorithmic bytes per processed (simulation, tet) entry of the batched
+    engine, counted as for one tet-period of the fused period kernel: the
+    reverse-face table (16) and, per species, the kept count (read 4, write
+    4), the four incoming and the four outgoing transfers (16 + 16) and the
+    cumulative face thresholds (16): 16 + 56 S."""
+    return 16 + 56 * S
 
 
 def make_workload(name: str):
@@ -73,30 +70,6 @@ def algorithmic_bytes_per_tet_period(S: int, R: int, masked: bool) -> int:
     (16) and the cumulative face thresholds (16); with reactions the tet
     volume (8) and, with a reaction mask, its bits (4)."""
     return 16 + 56 * S + (8 if R > 0 else 0) + (4 if masked else 0)
-
-
-def kernel_source_digest() -> str:
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1512_03126_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-    return h.hexdigest()[:16]
-
-
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
-    summary (profiles/<kernel>_<workload>.md), if it was taken on the
-    current kernel source."""
-    path = os.path.join(PROFILES, f"{kernel}_{workload}.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    d = re.search(r"kernel_source_digest:\s*([0-9a-f]+)", text)
-    if not m or not d or d.group(1) != kernel_source_digest():
-        return None
-    return float(m.group(1))
 
 
 def measured_peaks():
@@ -225,7 +198,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = bpt * T / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     roofline = {"kernel": "k_period", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("k_period", args.workload),
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "bytes_per_tet_period": bpt, "launch_us": round(per_launch_s * 1e6, 3),
                 "sampled_launches": kn, "peak_source": f"{peak_kind} hbm_gbs"}
 
@@ -369,6 +342,7 @@ def run_ensemble(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = rd.rdsplit_kernel_launches() - launches0
     steps1, proc1, kms, kn = rd.rdsplit_engine_stats(eng)
+    slot_times = rd.rdsplit_engine_slot_times(eng, n_inst)   # the last timed launch
     rd.rdsplit_engine_set_timing(eng, 0)
     clk = clocks.stop()
     if world > 1:
@@ -383,12 +357,16 @@ def run_ensemble(args, rank, world, local_rank):
     achieved = bpe * (entries / launches_per_step) / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     roofline = {"kernel": "k_engine_run", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic("k_engine_run", "ensemble"),
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "bytes_per_entry": bpe, "entries_per_launch": round(entries / launches_per_step, 1),
                 "launch_us": round(per_launch_s * 1e6, 3), "sampled_launches": kn,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "limit": "not HBM: DRAM moves ~2 B per entry (L2 serves the active tets); instruction issue at "
-                         "16 warps/SM and the per-period cluster barrier bound it (profiles/k_engine_run_ensemble.md)"}
+                "limit": "not HBM: DRAM moves ~2 B per entry (L2 serves the active tets); instruction issue "
+                         "and the per-period cluster barrier bound it"}
+
+    in_flight, csize, fit = rd.rdsplit_engine_schedule(eng)
+    tail = engine_tail(slot_times, periods, [w.mesh.n_tets for w in ws], in_flight)
+    tail.update({"cluster_ctas": csize, "clusters_fit": fit})
 
     # the plain form: each simulation through its own rdsplit_run
     plain = None
@@ -413,23 +391,26 @@ def run_ensemble(args, rank, world, local_rank):
     if not args.no_e2e:
         host_in = [torch.from_numpy(np.ascontiguousarray(w.counts)).pin_memory() for w in ws]
         host_out = [torch.empty_like(x).pin_memory() for x in host_in]
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for s, x in zip(sims, host_in):
-            rd.rdsplit_set_counts(s.h, x.numpy())
-            rd.rdsplit_set_time(s.h, 0.0, 0)
-        rd.rdsplit_ensemble_run([s.h for s in sims], [w.t_end for w in ws], seeds)
-        for s, y in zip(sims, host_out):
-            rd.rdsplit_get_counts(s.h, y.numpy())
-        e1.record(stream)
-        e1.synchronize()
-        ems = e0.elapsed_time(e1)
+        e_ms = []
+        for _ in range(max(3, min(args.steps, 5))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s, x in zip(sims, host_in):
+                rd.rdsplit_set_counts(s.h, x.numpy())
+                rd.rdsplit_set_time(s.h, 0.0, 0)
+            rd.rdsplit_ensemble_run([s.h for s in sims], [w.t_end for w in ws], seeds)
+            for s, y in zip(sims, host_out):
+                rd.rdsplit_get_counts(s.h, y.numpy())
+            e1.record(stream)
+            e1.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
         nb = sum(int(x.numel()) * 4 for x in host_in)
-        e2e = {"value": units * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb}
+        e_ms = D.max_over_ranks(sum(e_ms), dev) / len(e_ms) if world > 1 else sum(e_ms) / len(e_ms)
+        e2e = {"value": units * world / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb, "steps": max(3, min(args.steps, 5)), "ms_per_step": e_ms}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -466,11 +447,49 @@ def run_ensemble(args, rank, world, local_rank):
                    "processed_entries_per_step": entries, "mesh_generation_s": round(gen_s, 1),
                    "l2": "flushed between steps (256 MiB write); per step the ensemble state is 2.3 GB",
                    "parallelism": f"replicas x{world} (each rank its own ensemble, own seeds)"},
-        "roofline": roofline, "plain": plain,
+        "processed_entries_per_s": entries * args.steps * world / (total_ms / 1e3),
+        "roofline": roofline, "tail": tail, "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
         "serving": serving,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
     }
+
+
+def engine_tail(slot_times, periods, tets, in_flight: int) -> dict:
+    """How the engine's time splits, from each simulation's device-clock
+    start and end and its processed entries (one launch): the share of the
+    launch with fewer simulations running than clusters in flight, the mean
+    number running, the longest simulation, and a least-squares split of the
+    simulations' spans into a cost per period and a cost per entry."""
+    st = np.asarray(slot_times, dtype=np.float64)
+    ok = (st[:, 0] > 0) & (st[:, 1] >= st[:, 0])
+    if not ok.any():
+        return None
+    idx = np.nonzero(ok)[0]
+    st = st[ok]
+    P = np.asarray(periods, dtype=np.float64)[idx]
+    t0, t1 = st[:, 0].min(), st[:, 1].max()
+    ev = sorted([(a, 1) for a in st[:, 0]] + [(b, -1) for b in st[:, 1]])
+    busy, last, under, area, peak = 0, t0, 0.0, 0.0, 0
+    for t, d in ev:
+        if busy < in_flight:
+            under += t - last
+        area += busy * (t - last)
+        busy += d
+        peak = max(peak, busy)
+        last = t
+    span = st[:, 1] - st[:, 0]
+    i = int(np.argmax(span))
+    A = np.stack([P, st[:, 2]], axis=1)
+    coef, *_ = np.linalg.lstsq(A, span, rcond=None)
+    dur = t1 - t0 if t1 > t0 else 1.0
+    return {"launch_ms": dur / 1e6, "in_flight": in_flight, "max_running": int(peak),
+            "mean_running": area / dur, "frac_below_full": under / dur,
+            "sum_spans_ms": float(span.sum() / 1e6),
+            "us_per_period": float(coef[0] / 1e3), "ns_per_entry": float(coef[1]),
+            "longest_sim_ms": float(span[i] / 1e6), "longest_sim_periods": int(P[i]),
+            "longest_sim_tets": int(np.asarray(tets)[idx[i]]),
+            "last_start_ms": float((st[:, 0].max() - t0) / 1e6)}
 
 
 # ----------------------------------------------------------------- serving --

@@ -43,7 +43,8 @@ extern "C" {
 #define RDSPLIT_EINVAL (-1)    /* bad argument, malformed mesh or model */
 #define RDSPLIT_ENOMEM (-2)    /* device allocation failed or budget exceeded */
 #define RDSPLIT_ECUDA (-3)     /* a CUDA runtime call failed */
-#define RDSPLIT_ETIMEOUT (-4)  /* a bounded device-side wait expired */
+#define RDSPLIT_ETIMEOUT (-4)  /* reserved: no call returns it (the kernels wait
+                                  only at hardware barriers, never on a flag) */
 #define RDSPLIT_EOVERFLOW (-5) /* a count would exceed INT32_MAX, or a
                                   period would exceed the per-tet event cap */
 #define RDSPLIT_ESTATE (-6)    /* call out of order (e.g. run before set_model) */
@@ -204,7 +205,8 @@ int rdsplit_get_timing(rdsplit_mesh_t mesh, double* total_ms, int64_t* n_sampled
 
 /*
  * Batched engine: many independent simulations advanced by one persistent
- * kernel in which each thread block takes one simulation from a queue
+ * kernel in which each thread-block cluster (1, 2 or 4 CTAs, see
+ * rdsplit_engine_set_concurrency) takes one simulation from a queue
  * (largest first) and runs its periods itself, touching only tets that hold
  * molecules (or have a zero-order reaction switched on).  Realisations in
  * parallel are the embarrassingly parallel use of Sec. I; each simulation's
@@ -239,28 +241,35 @@ int rdsplit_engine_step(rdsplit_engine_t engine, int64_t n_steps);
 int rdsplit_engine_poll(rdsplit_engine_t engine, int32_t* slots, int32_t max, int32_t* n_out);
 int rdsplit_engine_active(rdsplit_engine_t engine, int32_t* n_slots, int64_t* n_tets);
 int rdsplit_engine_destroy(rdsplit_engine_t engine);
-/* Scheduling: `in_flight` simulations are processed at once (0 = one per
- * `cluster` SMs), each by a thread-block cluster of `cluster` CTAs (1, 2 or
- * 4; default 4) that share its work through distributed shared memory.
- * Fewer in flight keeps their working sets in L2. */
+/* Scheduling: `in_flight` simulations are processed at once (0 = as many
+ * clusters as fit on the GPU at once; never more than that), each by a
+ * thread-block cluster of `cluster` CTAs (1, 2 or 4; default 4) that share
+ * its work through distributed shared memory.  Fewer in flight keeps their
+ * working sets in L2. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
-/* Activity bitmaps (one bit per tet and period parity) are kept in the
- * distributed shared memory of a simulation's cluster when both fit in
- * `max_bytes` per CTA (0 ..= 163840; default 163840), else in global memory.
- * 0 forces global bitmaps.  Results do not depend on this setting. */
-int rdsplit_engine_set_bitmap_smem(rdsplit_engine_t engine, int32_t max_bytes);
 /* Profiling: time every engine launch with CUDA events (on != 0), and read
  * the periods advanced (maximum per step call, summed), the (simulation, tet)
  * entries processed, and the summed milliseconds / number of timed launches. */
 int rdsplit_engine_set_timing(rdsplit_engine_t engine, int32_t on);
 int rdsplit_engine_stats(rdsplit_engine_t engine, int64_t* steps, int64_t* processed,
                          double* timing_ms, int64_t* timing_n);
+/* Profiling: while timing is on, each launch records for every simulation it
+ * runs the device clock (%globaltimer, ns) when its cluster takes it and when
+ * it finishes its slice, and the (simulation, tet) entries it processed.
+ * Copies int64 [n][3] (start, end, entries) for slots 0 .. n-1, n =
+ * min(max_slots, engine slots); a slot not run since timing was switched on
+ * holds what it held before (0 initially). */
+int rdsplit_engine_slot_times(rdsplit_engine_t engine, int64_t* out, int32_t max_slots);
+/* The schedule of the last launch: simulations in flight (clusters
+ * launched), CTAs per cluster, and the number of clusters the occupancy
+ * query says fit on the GPU at once (the default in-flight count). */
+int rdsplit_engine_schedule(rdsplit_engine_t engine, int32_t* in_flight, int32_t* cluster, int32_t* max_active);
 int rdsplit_ensemble_run(int32_t n, const rdsplit_mesh_t* meshes, const double* t_end,
                          const uint64_t* seeds);
 
 /*
- * Allocation-free run (the paper has no counterpart; this is a deployment
- * variant of rdsplit_run).  Some callers cannot call cudaMalloc: code running
+ * Allocation-free run.  The paper has no counterpart: this is a deployment
+ * variant of rdsplit_run.  Some callers cannot call cudaMalloc: code running
  * inside a host application that owns all device memory (a plugin with a
  * fixed memory budget), or a real-time loop that must not stall on the
  * device synchronisation an allocation can cause.  This entry point performs
@@ -268,8 +277,8 @@ int rdsplit_ensemble_run(int32_t n, const rdsplit_mesh_t* meshes, const double* 
  * one static device array of RDSPLIT_STATIC_SCRATCH_BYTES that the library
  * reserves on each GPU that loads it, until the process exits.
  *
- * It runs Algorithm 1 exactly as rdsplit_run does (same kernels, same
- * results) on caller-owned memory:
+ * It runs the same period loop and kernels as rdsplit_run, with the same
+ * results, on caller-owned memory:
  *   d_adj, d_vol, d_face_area, d_centroid_dist   the mesh, in DEVICE memory,
  *                 same layout and rules as rdsplit_mesh_create
  *   n_species, D, n_reactions, lhs, rhs, k      the model, in HOST memory,

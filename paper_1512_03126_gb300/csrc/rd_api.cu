@@ -94,7 +94,6 @@ int check_err_impl(rdsplit_mesh* h, const char* where) {
     if (e & kErrFace) return fail(RDSPLIT_EINVAL, "%s: a face area or centroid distance is invalid", where);
     if (e & kErrOverflow) return fail(RDSPLIT_EOVERFLOW, "%s: a count exceeded INT32_MAX", where);
     if (e & kErrEventCap) return fail(RDSPLIT_EOVERFLOW, "%s: SSA event cap per tet and period exceeded", where);
-    if (e & kErrTimeout) return fail(RDSPLIT_ETIMEOUT, "%s: bounded device wait expired", where);
     if (e & kErrNegative) return fail(RDSPLIT_EINVAL, "%s: negative count", where);
     return fail(RDSPLIT_ECUDA, "%s: device error bits 0x%x", where, e);
 }

@@ -66,63 +66,42 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v));
 }
 
-// Position of the k-th (0-based) set bit of w; w has more than k set bits.
-__device__ __forceinline__ int select_bit(uint32_t w, uint32_t k) {
-    int pos = 0;
-#pragma unroll
-    for (int half = 16; half > 0; half >>= 1) {
-        const uint32_t low = (uint32_t)__popc(w & ((1u << half) - 1u));
-        if (k >= low) {
-            k -= low;
-            w >>= half;
-            pos += half;
-        }
-    }
-    return pos;
+// Device clock in nanoseconds (the global timer shared by all SMs).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// The lane whose word holds the warp's j-th active tet, given each lane's
-// exclusive prefix `before` of the set-bit counts (non-decreasing over the
-// lanes): the largest lane with before <= j.  Every lane must call it.
-__device__ __forceinline__ int owner_lane(uint32_t before, uint32_t j) {
-    int lo = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t b = __shfl_sync(0xffffffffu, before, lo + step);
-        if (b <= j) lo += step;
-    }
-    return lo;
-}
-
-constexpr int kGroup = 8;        // bitmap words per lane loaded at once
-constexpr int kRowStride = 136;  // shared bitmap words per row: 16 warps x 8, padded against bank conflicts
-constexpr int kMaxSharedBitsBytes = 160 * 1024;
-
-// Shared-memory words (both parities) a simulation of W bitmap words needs
-// on each CTA of a cluster of kc CTAs.
-inline int64_t shared_bits_words(int64_t W, int kc) {
-    const int64_t kw = (int64_t)kc * (kRunBlock / 32);
-    const int64_t rows = (W + 8 * kw - 1) / (8 * kw);
-    return 2 * rows * kRowStride;
+// Fire-and-forget OR into a global bitmap word.
+__device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v));
 }
 
 constexpr int kWarps = kRunBlock / 32;
-constexpr int kQueue = 64;   // deferred tets per warp
+constexpr int kGroup = 8;                   // bitmap columns (32 words each) a warp loads at once
+constexpr int kQueue = 64;                  // deferred tets per warp
+constexpr int kListCap = 32 * 32 + 32;      // active tets one column can add, plus a partial round
+constexpr int kDynSmemBytes = kWarps * kListCap * 4;
 
 // Shared memory of the engine kernel, at file scope so that the period
 // functions below address it directly.
 __shared__ int32_t s_item;                          // work-item index (first CTA of the cluster)
 __shared__ uint32_t s_total[2];                     // molecule total of a reaction-free simulation; [1]: too large
-__shared__ uint32_t s_wbuf[kWarps][kGroup * 32];    // per warp: the bitmap words of its current group
+__shared__ uint32_t s_wbuf[kWarps][kGroup * 32];    // per warp: the bitmap words of its current batch
 __shared__ int32_t s_slowq[kWarps][kQueue];         // per warp: tets deferred to the rounds with the full step
-extern __shared__ uint32_t s_bits[];                // [2][rows * kRowStride]: this CTA's runs of both bitmaps
+extern __shared__ int32_t s_list[];                 // [kWarps][kListCap]: per warp, active tets not yet run
 
-// Where one period stands for one warp: the light pass stops early when the
-// warp's queue could overflow and resumes at (g0, j0) after the queue is run.
+// Where one period stands for one warp.  The light pass stops early when the
+// warp's queue of deferred tets could overflow, and resumes after the queue
+// has been run: at batch g0, column kk (the batch's words are kept in s_wbuf
+// when `loaded`), with `cnt` active tets still in the warp's list.
 struct LightState {
     uint32_t bad;
     int32_t n_slow;      // tets in the warp's queue
-    int32_t g0, j0;      // resume point (group, round)
+    int32_t g0, kk;      // resume point (batch, column)
+    int32_t cnt;         // tets in the warp's list
+    int32_t loaded;      // the batch's words are in s_wbuf
     int32_t finished;
     unsigned long long done;
 };
@@ -130,23 +109,22 @@ struct LightState {
 // Everything a period pass derives from the slot descriptor and the period.
 template <int kC>
 struct PeriodView {
-    int T, S, W, rw, r, tstride;
-    bool in_smem, use_packed, more, exact;
+    int T, S, W, r, tstride;
+    bool use_packed, more, exact;
     double tau_k;
     float tau_kf;
     uint32_t period;
     const uint4* thr;
     int32_t* Ncur;
     int32_t* Nnext;
+    uint32_t* bcur;
+    uint32_t* bnext;
     int64_t cstride;
 
-    __device__ __forceinline__ PeriodView(const SlotDesc& d, int q, int32_t dyn_words, bool exact_) {
-        constexpr int kW = kC * kWarps;
+    __device__ __forceinline__ PeriodView(const SlotDesc& d, int q, bool exact_) {
         T = d.m.T;
         S = d.S;
         W = (T + 31) >> 5;
-        rw = (W + 8 * kW - 1) / (8 * kW) * kRowStride;
-        in_smem = 2 * rw <= dyn_words;
         r = (q - d.q0) & 1;
         const bool last = (q == d.P - 1) && d.last_short;
         tau_k = last ? d.tau_last : d.tau;
@@ -163,24 +141,15 @@ struct PeriodView {
         Ncur = inter ? d.N2 + r : d.N[r];
         Nnext = inter ? d.N2 + (r ^ 1) : d.N[r ^ 1];
         cstride = inter ? 2 : 1;
+        bcur = d.bits[r];
+        bnext = d.bits[r ^ 1];
         more = q + 1 < d.q1;
         exact = exact_;
     }
 
-    // Word wi of bitmap p: in the shared memory of the CTA whose warp scans
-    // it, or in global memory.
-    __device__ __forceinline__ uint32_t* word_ptr(const SlotDesc& d, int p, int wi) const {
-        constexpr int kW = kC * kWarps;
-        if (!in_smem) return d.bits[p] + wi;
-        const int run = wi >> 3;
-        const int owner = run % kW;
-        uint32_t* a = s_bits + p * rw + (run / kW) * kRowStride + (owner % kWarps) * 8 + (wi & 7);
-        if (kC == 1) return a;
-        return cooperative_groups::this_cluster().map_shared_rank(a, owner / kWarps);
-    }
-
     // Transfer of one tet's molecules (kept and leaving) into the next
-    // counts, and its bits in the next bitmap.
+    // counts, and its bits in the next bitmap (fire-and-forget ORs: a bit
+    // set twice is set once).
     template <int SA, bool kReact>
     __device__ __forceinline__ uint32_t scatter(const SlotDesc& d, const ModelParams& mp, int t, const int4& sr,
                                                 const int32_t* N, const int4* o) const {
@@ -217,145 +186,166 @@ struct PeriodView {
             }
         }
         if (more) {
-            if (keep) atomicOr(word_ptr(d, r ^ 1, t >> 5), 1u << (t & 31));
+            if (keep) red_or(bnext + (t >> 5), 1u << (t & 31));
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 if (!send[f]) continue;
                 const int u = nbr[f] >> 2;
-                atomicOr(word_ptr(d, r ^ 1, u >> 5), 1u << (u & 31));
+                red_or(bnext + (u >> 5), 1u << (u & 31));
             }
         }
         return bad;
     }
 };
 
-// The light pass of one period for one warp: scan the warp's bitmap words,
-// run every tet that needs no non-inlined sampler (step_is_light) with the
-// call-free step, and queue the others.  Kept out of line, and free of calls,
-// so that the compiler allocates its registers without the double-precision
-// samplers' demands (with them in the same loop nest it spills the round's
-// live values to local memory, which cost 5x in time).  Returns early, with
-// a resume point, when the next round could overflow the queue.
+// The light pass of one period for one warp.  The bitmap is dealt to the
+// cluster's kW warps in runs of 8 words (256 tets, one 32-byte sector): run
+// r goes to warp r mod kW, so the active tets of a region are spread over
+// all warps.  A column is 4 runs of a warp (32 words, one per lane); a warp
+// loads kGroup of its columns at once, clears them for their next use, and
+// appends the set bits of each column to its list in shared memory
+// (a prefix sum of the lanes' popcounts gives each lane its place); whenever
+// the list holds 32 tets, one round takes them, one per lane.  A round runs
+// every tet that needs no non-inlined sampler (step_is_light) with the
+// call-free step, and queues the others for the slow pass.  Kept out of
+// line, and free of calls, so that the compiler allocates its registers
+// without the double-precision samplers' demands.  Returns early, with a
+// resume point, when the next round could overflow the queue.
 template <int SA, bool kReact, int kC>
 __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, const ModelParams* __restrict__ mpp,
-                                              int q, int32_t dyn_words, bool exact, uint32_t* err, bool resuming,
-                                              int g_start, int j_start) {
+                                              int q, bool exact, uint32_t* err, LightState st) {
     constexpr unsigned kAll = 0xffffffffu;
     constexpr int kW = kC * kWarps;
     const SlotDesc& d = *dp;
     const ModelParams& mp = *mpp;
-    const PeriodView<kC> v(d, q, dyn_words, exact);
+    const PeriodView<kC> v(d, q, exact);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int rank = kC > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
     const int gw = rank * kWarps + warp;
     const unsigned lane_lt = (1u << lane) - 1u;
     uint32_t* wb = s_wbuf[warp];
+    int32_t* list = s_list + warp * kListCap;
     int32_t* slowq = s_slowq[warp];
-    // this warp's runs of the current bitmap (row stride kRowStride in
-    // shared memory) or the global bitmap
-    uint32_t* bcur = v.in_smem ? s_bits + v.r * v.rw + warp * 8 : d.bits[v.r];
-    LightState st{0u, 0, 0, 0, 1, 0ull};
-    for (int g0 = g_start; g0 < v.W; g0 += kGroup * 32 * kW) {
-        // a resumed group's words are already in wb (and cleared in the bitmap)
-        const bool resume = resuming && g0 == g_start;
-        if (!resume) {
+    st.bad = 0u;
+    st.n_slow = 0;
+    st.done = 0ull;
+
+    // one round: the tets t of the live lanes
+    auto round = [&](int t, bool live) {
+        uint32_t heavy = 0;
+        int32_t N[SA];
+        int4 o[SA];
+        int4 sr = make_int4(-1, -1, -1, -1);
+        uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+        bool light = false;
+        if (live) {
+            // the tet's record and counts, loaded together
+            sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
+            if (v.use_packed) pre = d.packed[2 * t + 1];
+#pragma unroll
+            for (int s = 0; s < SA; ++s) {
+                if (s >= v.S) break;
+                N[s] = v.Ncur[((int64_t)s * v.T + t) * v.cstride];
+            }
+            light = step_is_light<SA, kReact>(d.m, mp, v.period, v.tau_kf, d.seed, t, v.S, N);
+        }
+        const unsigned slow_mask = __ballot_sync(kAll, live && !light);
+        if (live && !light) slowq[st.n_slow + __popc(slow_mask & lane_lt)] = t;
+        st.n_slow += __popc(slow_mask);
+        if (light) {
+#pragma unroll
+            for (int s = 0; s < SA; ++s) {
+                if (s >= v.S) break;
+                v.Ncur[((int64_t)s * v.T + t) * v.cstride] = 0;
+            }
+            st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
+                                                 &heavy, err, v.tstride, v.use_packed, pre);
+        }
+        warp_split<SA>(heavy, d.seed, v.period, t, v.thr, v.T, N, o, v.tstride, v.use_packed, pre);
+        if (light) st.bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
+    };
+
+    // the word of lane `lane` in column kk of batch b: run j of this warp
+    // (8 words, one 32-byte sector), runs dealt round-robin over the warps
+    auto word_of = [&](int b, int kk) {
+        const int j = (b * kGroup + kk) * 4 + (lane >> 3);
+        return (gw + j * kW) * 8 + (lane & 7);
+    };
+    int b = st.g0;
+    for (;; ++b) {
+        if (!st.loaded) {
+            if ((gw + b * kGroup * 4 * kW) * 8 >= v.W) break;
             uint32_t wds[kGroup];
 #pragma unroll
             for (int kk = 0; kk < kGroup; ++kk) {
-                const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
-                const int li = v.in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
-                wds[kk] = wi < v.W ? bcur[li] : 0u;
+                const int wi = word_of(b, kk);
+                wds[kk] = wi < v.W ? v.bcur[wi] : 0u;
             }
 #pragma unroll
             for (int kk = 0; kk < kGroup; ++kk) {
-                const int wi = g0 + ((kk * 4 + (lane >> 3)) * kW + gw) * 8 + (lane & 7);
-                const int li = v.in_smem ? (g0 / (8 * kW) + kk * 4 + (lane >> 3)) * kRowStride + (lane & 7) : wi;
-                if (wds[kk]) bcur[li] = 0u;
+                const int wi = word_of(b, kk);
+                if (wds[kk]) v.bcur[wi] = 0u;
                 wb[kk * 32 + lane] = wds[kk];
             }
             __syncwarp();
+            st.loaded = 1;
+            st.kk = 0;
         }
-        uint32_t c = 0;
+        for (int kk = st.kk; kk < kGroup; ++kk) {
+            // full rounds first, so that one more column always fits the list
+            while (st.cnt >= 32) {
+                if (st.n_slow > kQueue - 32) {
+                    st.g0 = b;
+                    st.kk = kk;
+                    st.finished = 0;
+                    return st;
+                }
+                const int t = list[st.cnt - 32 + lane];
+                __syncwarp();
+                st.cnt -= 32;
+                round(t, true);
+            }
+            uint32_t w = wb[kk * 32 + lane];
+            if (__any_sync(kAll, w != 0u)) {
+                const uint32_t c = (uint32_t)__popc(w);
+                uint32_t inc = c;
 #pragma unroll
-        for (int kk = 0; kk < kGroup; ++kk) c += (uint32_t)__popc(wb[kk * 32 + lane]);
-        uint32_t inc = c;
-#pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-            const uint32_t y = __shfl_up_sync(kAll, inc, dd);
-            if (lane >= dd) inc += y;
+                for (int dd = 1; dd < 32; dd <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kAll, inc, dd);
+                    if (lane >= dd) inc += y;
+                }
+                const int total = (int)__shfl_sync(kAll, inc, 31);
+                int at = st.cnt + (int)(inc - c);
+                const int base = word_of(b, kk) * 32;
+                while (w) {
+                    const int bit = __ffs(w) - 1;
+                    list[at++] = base + bit;
+                    w &= w - 1u;
+                }
+                __syncwarp();
+                st.cnt += total;
+                st.done += (unsigned long long)total;
+            }
         }
-        const uint32_t n_act = __shfl_sync(kAll, inc, 31);
-        const uint32_t before = inc - c;
-        if (!resume) st.done += n_act;
-        for (uint32_t j0 = resume ? (uint32_t)j_start : 0u; j0 < n_act; j0 += 32) {
-            const uint32_t j = j0 + (uint32_t)lane;
-            const bool live = j < n_act;
-            const uint32_t jj = live ? j : n_act - 1u;
-            const int own = owner_lane(before, jj);
-            uint32_t rel = jj - __shfl_sync(kAll, before, own);
-            // the owner's word that holds bit number rel
-            int kw = 0;
-            uint32_t ww = 0;
-            bool found = false;
-#pragma unroll
-            for (int kk = 0; kk < kGroup; ++kk) {
-                const uint32_t w = wb[kk * 32 + own];
-                const uint32_t pc = (uint32_t)__popc(w);
-                if (!found) {
-                    if (rel < pc) {
-                        found = true;
-                        kw = kk;
-                        ww = w;
-                    } else {
-                        rel -= pc;
-                    }
-                }
-            }
-            const int t = live ? (g0 + ((kw * 4 + (own >> 3)) * kW + gw) * 8 + (own & 7)) * 32 + select_bit(ww, rel)
-                               : 0;
-            uint32_t heavy = 0;
-            int32_t N[SA];
-            int4 o[SA];
-            int4 sr = make_int4(-1, -1, -1, -1);
-            uint4 pre = make_uint4(0u, 0u, 0u, 0u);
-            bool light = false;
-            if (live) {
-                // the tet's record and counts, loaded together
-                sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
-                if (v.use_packed) pre = d.packed[2 * t + 1];
-#pragma unroll
-                for (int s = 0; s < SA; ++s) {
-                    if (s >= v.S) break;
-                    N[s] = v.Ncur[((int64_t)s * v.T + t) * v.cstride];
-                }
-                light = step_is_light<SA, kReact>(d.m, mp, v.period, v.tau_kf, d.seed, t, v.S, N);
-            }
-            const unsigned slow_mask = __ballot_sync(kAll, live && !light);
-            if (st.n_slow + __popc(slow_mask) > kQueue) {
-                // no side effect of this round has happened yet: stop here
-                st.g0 = g0;
-                st.j0 = (int)j0;
-                st.finished = 0;
-                __syncwarp();   // the queue is read by other lanes next
-                return st;
-            }
-            if (live && !light) slowq[st.n_slow + __popc(slow_mask & lane_lt)] = t;
-            st.n_slow += __popc(slow_mask);
-            if (light) {
-#pragma unroll
-                for (int s = 0; s < SA; ++s) {
-                    if (s >= v.S) break;
-                    v.Ncur[((int64_t)s * v.T + t) * v.cstride] = 0;
-                }
-                st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N,
-                                                     o, &heavy, err, v.tstride, v.use_packed, pre);
-            }
-            warp_split<SA>(heavy, d.seed, v.period, t, v.thr, v.T, N, o, v.tstride, v.use_packed, pre);
-            if (light) st.bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
-        }
-        __syncwarp();   // wb is rewritten by the next group
+        st.loaded = 0;
+        st.kk = 0;
     }
+    // the rest of the list, in rounds of up to 32
+    while (st.cnt > 0) {
+        if (st.n_slow > kQueue - 32) {
+            st.g0 = b;
+            st.finished = 0;
+            return st;
+        }
+        const int n = st.cnt < 32 ? st.cnt : 32;
+        const int t = lane < n ? list[st.cnt - n + lane] : 0;
+        __syncwarp();
+        st.cnt -= n;
+        round(t, lane < n);
+    }
+    st.g0 = b;
+    st.finished = 1;
     return st;
 }
 
@@ -363,10 +353,10 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
 // the full per-tet step: reactions and the non-inlined samplers.
 template <int SA, bool kReact, int kC>
 __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, const ModelParams* __restrict__ mpp, int q,
-                                           int32_t dyn_words, bool exact, uint32_t* err, int n) {
+                                           bool exact, uint32_t* err, int n) {
     const SlotDesc& d = *dp;
     const ModelParams& mp = *mpp;
-    const PeriodView<kC> v(d, q, dyn_words, exact);
+    const PeriodView<kC> v(d, q, exact);
     const int lane = threadIdx.x & 31;
     const int32_t* slowq = s_slowq[threadIdx.x >> 5];
     uint32_t bad = 0;
@@ -402,22 +392,12 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
 // first CTA owns the work-item index; the others read it through distributed
 // shared memory.  cluster.sync() (a hardware barrier) separates periods.
 //
-// The tets to visit in a period are the set bits of that period's bitmap.
-// The words are dealt to the cluster's kW warps in runs of 8 (256 tets, one
-// 32-byte sector): run r of a group goes to warp r mod kW, so the active tets
-// of a dense region are spread over all warps, and each lane loads kGroup
-// words at once.  The warp hands the set bits of its 32 x kGroup words to its
-// lanes, 32 at a time, by a prefix sum of the lanes' popcounts, an owner-lane
-// search and a select-the-k-th-bit step.  Each visited word is cleared for
-// its next use; a tet that keeps or receives molecules sets its bit in the
-// other parity's bitmap (an atomic OR, which is idempotent, so no membership
-// test and no list are needed).  At the end of a slice both bitmaps are zero.
-//
-// The bitmaps live in distributed shared memory when they fit (both parities
-// in kMaxSharedBitsBytes per CTA): the run of 8 words that warp g scans is
-// kept in the shared memory of warp g's CTA, so the scan reads local shared
-// memory and the bit sets are shared-memory atomics on the owning CTA, with
-// no L2 traffic.  Larger simulations use the global bitmaps.
+// The tets to visit in a period are the set bits of that period's bitmap
+// (global memory, one bit per tet, one bitmap per period parity).  Each
+// visited word is cleared for its next use; a tet that keeps or receives
+// molecules sets its bit in the other parity's bitmap (an OR, which is
+// idempotent, so no membership test and no list are needed).  At the end of
+// a slice both bitmaps are zero.
 //
 // Count adds return the old value to detect a count above 2^31-1, except in
 // a simulation without reactions whose molecules sum to at most 2^31-1: no
@@ -425,10 +405,10 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
 template <int SA, bool kReact, int kC>
 __global__ void __launch_bounds__(kRunBlock, 1)
 k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__ mps, const int32_t* __restrict__ order,
-             int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed, int32_t dyn_words) {
+             int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed,
+             unsigned long long* times) {
     namespace cg = cooperative_groups;
     constexpr unsigned kAll = 0xffffffffu;
-    constexpr int kW = kC * kWarps;   // warps per simulation
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
     int32_t* item = kC > 1 ? cluster.map_shared_rank(&s_item, 0) : &s_item;
@@ -453,6 +433,11 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         csync();
         if (k >= n_items) break;
         const int slot = order[k];
+        if (times && rank == 0 && threadIdx.x == 0) {
+            times[4 * slot] = globaltimer_ns();
+            times[4 * slot + 2] = 0ull;
+        }
+        unsigned long long item_done = 0;
         const SlotDesc& d = descs[slot];   // read-only; fields are loaded where used
         const ModelParams& mp = mps[slot];
         const int T = d.m.T;
@@ -460,10 +445,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         const int W = (T + 31) >> 5;
         const bool inter = d.N2 != nullptr;   // one species, interleaved counts
         const bool conserved = mp.R == 0;     // molecules are only moved
-        const PeriodView<kC> v0(d, d.q0, dyn_words, true);
         uint32_t bad = 0;
-        if (v0.in_smem)
-            for (int i = threadIdx.x; i < v0.rw; i += kRunBlock) s_bits[v0.rw + i] = 0u;   // bitmap 1 starts empty
         // initial bitmap: occupied tets and tets with a zero-order reaction on
         // (whole words, written by the first lane of each 32-tet run); and the
         // molecule total of a reaction-free simulation
@@ -481,7 +463,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                 }
             }
             const uint32_t word = __ballot_sync(kAll, occ);
-            if (lane == 0 && (t >> 5) < W) *v0.word_ptr(d, 0, t >> 5) = word;
+            if (lane == 0 && (t >> 5) < W) d.bits[0][t >> 5] = word;
         }
         if (conserved) {
 #pragma unroll
@@ -499,19 +481,13 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         for (int q = d.q0; q < d.q1; ++q) {
             csync();   // the previous period's adds and bits are complete
             if (q == d.q0) exact = !conserved || total[1] != 0u;
-            int g0 = 0, j0 = 0;
-            bool resuming = false;
+            LightState st{0u, 0, 0, 0, 0, 0, 0, 0ull};
             for (;;) {
-                const LightState st = light_pass<SA, kReact, kC>(descs + slot, mps + slot, q, dyn_words, exact, err,
-                                                                 resuming, g0, j0);
+                st = light_pass<SA, kReact, kC>(descs + slot, mps + slot, q, exact, err, st);
                 bad |= st.bad;
-                done += st.done;
-                if (st.n_slow > 0) bad |= slow_pass<SA, kReact, kC>(descs + slot, mps + slot, q, dyn_words, exact, err,
-                                                                    st.n_slow);
+                item_done += st.done;
+                if (st.n_slow > 0) bad |= slow_pass<SA, kReact, kC>(descs + slot, mps + slot, q, exact, err, st.n_slow);
                 if (st.finished) break;
-                g0 = st.g0;
-                j0 = st.j0;
-                resuming = true;
             }
         }
         csync();   // every add of the slice is complete
@@ -522,8 +498,13 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
             for (int t = rank * kRunBlock + threadIdx.x; t < T; t += kC * kRunBlock) d.N[0][t] = d.N2[2 * t + half];
         }
         if (bad) atomicOr(err, bad);
+        done += item_done;
+        if (times) {
+            if (lane == 0 && item_done) atomicAdd(times + 4 * slot + 2, item_done);
+            if (rank == 0 && threadIdx.x == 0) times[4 * slot + 1] = globaltimer_ns();
+        }
     }
-    // entries processed: counted by lane 0 of each warp (n_act is warp-uniform)
+    // entries processed: counted by lane 0 of each warp (warp-uniform)
     if (lane == 0 && done) atomicAdd(processed, done);
 }
 
@@ -540,23 +521,37 @@ void launch_pack(int32_t T, const int4* src, const uint4* thr, uint4* out, cudaS
     note_launch();
 }
 
+// Arguments of one engine launch.  `clusters` is the number of simulations
+// to keep in flight (0: as many clusters as fit on the GPU at once); the
+// launch never asks for more clusters than fit, since a persistent cluster
+// that cannot be resident would only start when another one has finished.
+struct EngineLaunch {
+    const SlotDesc* descs;
+    const ModelParams* mps;
+    const int32_t* order;
+    int32_t n_items;
+    int32_t* head;
+    uint32_t* err;
+    unsigned long long* processed;
+    unsigned long long* times;
+    cudaStream_t st;
+    int sms;
+    int clusters;
+    int used = 0;         // clusters launched
+    int max_active = 0;   // clusters resident at once (occupancy query)
+};
+
 template <int SA, bool R, int C>
-cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParams* mps, const int32_t* order,
-                           int32_t n_items, int32_t* head, uint32_t* err, unsigned long long* processed,
-                           int32_t dyn_words, cudaStream_t st) {
-    cudaError_t ce = cudaFuncSetAttribute(k_engine_run<SA, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kMaxSharedBitsBytes);
+cudaError_t launch_cluster(EngineLaunch& L) {
+    auto kern = k_engine_run<SA, R, C>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemBytes);
     if (ce != cudaSuccess) return ce;
-    if (C == 1) {
-        k_engine_run<SA, R, C><<<clusters, kRunBlock, (size_t)dyn_words * 4, st>>>(descs, mps, order, n_items, head,
-                                                                                  err, processed, dyn_words);
-        return cudaGetLastError();
-    }
+    const size_t dyn = (size_t)kDynSmemBytes;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(clusters * C, 1, 1);
+    cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(kRunBlock, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)dyn_words * 4;
-    cfg.stream = st;
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = L.st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
@@ -564,24 +559,35 @@ cudaError_t launch_cluster(int clusters, const SlotDesc* descs, const ModelParam
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_engine_run<SA, R, C>, descs, mps, order, n_items, head, err, processed,
-                              dyn_words);
+    int fit = 0;
+    if (C == 1) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRunBlock, dyn) == cudaSuccess)
+            fit = per_sm * L.sms;
+    } else if (cudaOccupancyMaxActiveClusters(&fit, kern, &cfg) != cudaSuccess) {
+        fit = 0;
+    }
+    cudaGetLastError();
+    if (fit <= 0) fit = std::max(1, L.sms / C);
+    L.max_active = fit;
+    int n = L.clusters > 0 ? std::min(L.clusters, fit) : fit;
+    n = std::max(1, std::min(n, L.n_items));
+    L.used = n;
+    if (C == 1) {
+        kern<<<n, kRunBlock, dyn, L.st>>>(L.descs, L.mps, L.order, L.n_items, L.head, L.err, L.processed,
+                                          L.times);
+        return cudaGetLastError();
+    }
+    cfg.gridDim = dim3(n * C, 1, 1);
+    return cudaLaunchKernelEx(&cfg, kern, L.descs, L.mps, L.order, L.n_items, L.head, L.err, L.processed,
+                              L.times);
 }
 
 template <int SA>
-cudaError_t launch_run_sa(bool react, int cluster, int clusters, const SlotDesc* descs, const ModelParams* mps,
-                          const int32_t* order, int32_t n_items, int32_t* head, uint32_t* err,
-                          unsigned long long* processed, int32_t dyn_words, cudaStream_t st) {
-    if (cluster >= 4) {
-        if (react) return launch_cluster<SA, true, 4>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
-        return launch_cluster<SA, false, 4>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
-    }
-    if (cluster == 2) {
-        if (react) return launch_cluster<SA, true, 2>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
-        return launch_cluster<SA, false, 2>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
-    }
-    if (react) return launch_cluster<SA, true, 1>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
-    return launch_cluster<SA, false, 1>(clusters, descs, mps, order, n_items, head, err, processed, dyn_words, st);
+cudaError_t launch_run_sa(bool react, int cluster, EngineLaunch& L) {
+    if (cluster >= 4) return react ? launch_cluster<SA, true, 4>(L) : launch_cluster<SA, false, 4>(L);
+    if (cluster == 2) return react ? launch_cluster<SA, true, 2>(L) : launch_cluster<SA, false, 2>(L);
+    return react ? launch_cluster<SA, true, 1>(L) : launch_cluster<SA, false, 1>(L);
 }
 
 }  // namespace
@@ -596,6 +602,7 @@ struct rdsplit_engine {
     int32_t* d_head = nullptr;
     uint32_t* err = nullptr;
     unsigned long long* processed = nullptr;  // (slot, tet) entries processed so far
+    unsigned long long* d_times = nullptr;    // [max_slots][4] start, end (ns), entries of each slot's last slice
     int64_t launches = 0;                     // persistent launches issued
     int64_t steps = 0;                        // periods advanced, summed over step calls
     int32_t timing = 0;                       // time every launch with CUDA events
@@ -603,9 +610,10 @@ struct rdsplit_engine {
     double timing_ms = 0.0;
     int64_t timing_n = 0;
     int sms = 1;
-    int32_t concurrency = 0;                  // simulations in flight (0 = default)
+    int32_t concurrency = 0;                  // simulations in flight (0 = as many as fit)
+    int32_t last_in_flight = 0;               // clusters of the last launch
+    int32_t last_max_active = 0;              // clusters that fit at once in the last launch
     int32_t cluster = 4;                      // CTAs per simulation (1, 2 or 4)
-    int32_t bitmap_smem = kMaxSharedBitsBytes;  // shared memory per CTA for activity bitmaps (0: global only)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
     std::vector<int32_t> slot_q;              // local periods done
@@ -616,7 +624,7 @@ struct rdsplit_engine {
     ~rdsplit_engine() {
         for (cudaEvent_t x : ev)
             if (x) cudaEventDestroy(x);
-        void* ps[] = {d_desc, d_mp, d_order, d_head, err, processed};
+        void* ps[] = {d_desc, d_mp, d_order, d_head, err, processed, d_times};
         for (void* p : ps) rdapi::dev_free(p);
     }
 };
@@ -661,7 +669,9 @@ void plan_periods(double t, double tau, double t_end, int64_t* P, double* tau_la
 void finish_slot(rdsplit_engine* e, int slot) {
     rdsplit_mesh* h = e->slot_mesh[slot];
     const SlotDesc& d = e->h_desc[slot];
-    h->t = e->slot_t_end[slot];
+    // a simulation added with t_end at or before its time ran no period and
+    // keeps its time, as rdsplit_run would
+    if (d.P > 0) h->t = e->slot_t_end[slot];
     h->period = (int64_t)d.period0 + d.P;
     e->active_tets -= h->T;
     e->slot_mesh[slot] = nullptr;
@@ -686,7 +696,8 @@ int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_en
     e->d_head = (int32_t*)rdapi::dev_alloc(sizeof(int32_t));
     e->err = (uint32_t*)rdapi::dev_alloc(sizeof(uint32_t));
     e->processed = (unsigned long long*)rdapi::dev_alloc(sizeof(unsigned long long));
-    if (!e->d_desc || !e->d_mp || !e->d_order || !e->d_head || !e->err || !e->processed) {
+    e->d_times = (unsigned long long*)rdapi::dev_alloc(sizeof(unsigned long long) * 4 * max_slots);
+    if (!e->d_desc || !e->d_mp || !e->d_order || !e->d_head || !e->err || !e->processed || !e->d_times) {
         delete e;
         return rdapi::fail(RDSPLIT_ENOMEM, "rdsplit_engine_create: device allocation failed");
     }
@@ -698,6 +709,7 @@ int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_en
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaMemsetAsync(e->processed, 0, sizeof(unsigned long long), e->stream) != cudaSuccess ||
+        cudaMemsetAsync(e->d_times, 0, sizeof(unsigned long long) * 4 * max_slots, e->stream) != cudaSuccess ||
         cudaMemsetAsync(e->err, 0, sizeof(uint32_t), e->stream) != cudaSuccess) {
         cudaGetLastError();
         delete e;
@@ -841,28 +853,23 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     }
     const int n_items = (int)order.size();
     const int csize = e->cluster;
-    // shared-memory bitmaps: room for the largest simulation that fits
-    int64_t dyn_words = 0;
-    for (int32_t s : items) {
-        const int64_t need = shared_bits_words((e->slot_mesh[s]->T + 31) / 32, csize);
-        if (need * 4 <= e->bitmap_smem) dyn_words = std::max(dyn_words, need);
-    }
-    // default: one CTA per SM (38 clusters of 4 on 152 SMs).  More
-    // simulations in flight than that spill their scattered working sets out
-    // of L2 (152 one-CTA simulations run 25% slower than 38 four-CTA ones).
-    const int in_flight = e->concurrency > 0 ? e->concurrency : std::max(1, e->sms / std::max(1, csize));
-    const int clusters = std::min(n_items, in_flight);
+    // default: as many clusters as can be resident at once (one CTA per SM
+    // where the GPCs allow it).  More simulations in flight than that would
+    // spill their scattered working sets out of L2.
     if (e->timing && !e->ev[0]) {
         cudaEventCreate(&e->ev[0]);
         cudaEventCreate(&e->ev[1]);
     }
     if (e->timing) cudaEventRecord(e->ev[0], st);
-    int32_t* ord = e->d_order;
-    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
-    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
-    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
-    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
-    else ce = launch_run_sa<kMaxS>(react, csize, clusters, e->d_desc, e->d_mp, ord, n_items, e->d_head, e->err, e->processed, (int32_t)dyn_words, st);
+    EngineLaunch L{e->d_desc, e->d_mp, e->d_order, n_items, e->d_head, e->err, e->processed,
+                   e->timing ? e->d_times : nullptr, st, e->sms, e->concurrency};
+    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, L);
+    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, L);
+    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, L);
+    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, L);
+    else ce = launch_run_sa<kMaxS>(react, csize, L);
+    e->last_in_flight = L.used;
+    e->last_max_active = L.max_active;
     if (e->timing) cudaEventRecord(e->ev[1], st);
     note_launch();
     e->launches += 1;
@@ -923,11 +930,11 @@ int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_
     return RDSPLIT_OK;
 }
 
-int rdsplit_engine_set_bitmap_smem(rdsplit_engine_t e, int32_t max_bytes) {
-    if (!e || max_bytes < 0 || max_bytes > kMaxSharedBitsBytes)
-        return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_bitmap_smem: max_bytes must be in [0, %d]",
-                           kMaxSharedBitsBytes);
-    e->bitmap_smem = max_bytes;
+int rdsplit_engine_schedule(rdsplit_engine_t e, int32_t* in_flight, int32_t* cluster, int32_t* max_active) {
+    if (!e) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_schedule: NULL engine");
+    if (in_flight) *in_flight = e->last_in_flight;
+    if (cluster) *cluster = e->cluster;
+    if (max_active) *max_active = e->last_max_active;
     return RDSPLIT_OK;
 }
 
@@ -953,6 +960,23 @@ int rdsplit_engine_stats(rdsplit_engine_t e, int64_t* steps, int64_t* processed,
     if (processed) *processed = (int64_t)p;
     if (timing_ms) *timing_ms = e->timing_ms;
     if (timing_n) *timing_n = e->timing_n;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_slot_times(rdsplit_engine_t e, int64_t* out, int32_t max_slots) {
+    if (!e || !out || max_slots < 0)
+        return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_slot_times: bad argument");
+    const int32_t n = std::min(max_slots, e->max_slots);
+    std::vector<unsigned long long> buf(4 * (size_t)n);
+    cudaError_t ce = cudaMemcpyAsync(buf.data(), e->d_times, sizeof(unsigned long long) * 4 * (size_t)n,
+                                     cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    for (int32_t i = 0; ce == cudaSuccess && i < n; ++i)
+        for (int k = 0; k < 3; ++k) out[3 * i + k] = (int64_t)buf[4 * i + k];
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return rdapi::fail(RDSPLIT_ECUDA, "rdsplit_engine_slot_times: %s", cudaGetErrorString(ce));
+    }
     return RDSPLIT_OK;
 }
 

@@ -18,7 +18,6 @@ enum : uint32_t {
     kErrNegative = 1u << 4,      // negative count (input or invariant)
     kErrOverflow = 1u << 5,      // a count would exceed INT32_MAX
     kErrEventCap = 1u << 6,      // more SSA events in one tet-period than the cap
-    kErrTimeout = 1u << 7,       // a bounded device wait expired
 };
 
 // Chemistry, passed by value to kernels (lives in the constant bank).

@@ -67,8 +67,9 @@ def _declare(L):
         "rdsplit_zeta_histogram": ([vp, i32, vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
         "rdsplit_set_transfer_rule": ([vp, i32], C.c_int),
         "rdsplit_engine_set_concurrency": ([vp, i32, i32], C.c_int),
-        "rdsplit_engine_set_bitmap_smem": ([vp, i32], C.c_int),
         "rdsplit_engine_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)], C.c_int),
+        "rdsplit_engine_slot_times": ([vp, vp, i32], C.c_int),
+        "rdsplit_engine_schedule": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "rdsplit_run_static": ([i32, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, dbl, vp,
                                 C.POINTER(dbl), C.POINTER(i64), dbl, u64, vp], C.c_int),
         "rdsplit_get_timing": ([vp, C.POINTER(dbl), C.POINTER(i64)], C.c_int),
@@ -280,10 +281,6 @@ def rdsplit_engine_set_concurrency(e, in_flight: int, cluster: int = 4):
     _check(lib().rdsplit_engine_set_concurrency(e, int(in_flight), int(cluster)))
 
 
-def rdsplit_engine_set_bitmap_smem(e, max_bytes: int):
-    _check(lib().rdsplit_engine_set_bitmap_smem(e, int(max_bytes)))
-
-
 def rdsplit_engine_set_timing(e, stride: int):
     _check(lib().rdsplit_engine_set_timing(e, int(stride)))
 
@@ -293,6 +290,22 @@ def rdsplit_engine_stats(e):
     st, pr, ms, n = C.c_int64(), C.c_int64(), C.c_double(), C.c_int64()
     _check(lib().rdsplit_engine_stats(e, C.byref(st), C.byref(pr), C.byref(ms), C.byref(n)))
     return st.value, pr.value, ms.value, n.value
+
+
+def rdsplit_engine_slot_times(e, n_slots: int):
+    """int64 [n_slots][3]: device-clock start and end (ns) and entries
+    processed of each slot's last timed slice."""
+    out = np.zeros((int(n_slots), 3), np.int64)
+    _check(lib().rdsplit_engine_slot_times(e, _ptr(out), int(n_slots)))
+    return out
+
+
+def rdsplit_engine_schedule(e):
+    """(simulations in flight, CTAs per cluster, clusters that fit at once)
+    of the last launch."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().rdsplit_engine_schedule(e, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def rdsplit_ensemble_run(meshes, t_end, seeds):

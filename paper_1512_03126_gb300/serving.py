@@ -9,10 +9,12 @@ join at the next slice, finished ones leave and free their memory.  A
 request's latency is its completion time minus its arrival time (queueing,
 upload, simulation and read-back included).
 
-Large requests (n_tets * n_species at or above `dense_threshold`) do better
-with the whole GPU than with one engine cluster: they go to a dense lane, a
-worker thread that runs them one after another with rdsplit_run on its own
-CUDA stream, overlapping the engine's launches on the other stream.
+Requests with n_tets * n_species at or above `dense_threshold` can instead
+go to a dense lane: `dense_lanes` worker threads, each running its requests
+one after another with rdsplit_run (every tet every period, the whole GPU)
+on its own CUDA stream, overlapping the engine's launches and each other.
+Their device memory counts against the same budget, reserved at admission
+and released when they finish.
 
 Each simulation's random streams are keyed by its own seed, period index and
 canonical tet ids, so its result is the same whether it runs alone or mixed
@@ -57,11 +59,17 @@ class Server:
 
     def __init__(self, budget_bytes: float = 150e9, max_slots: int = 128, slice_periods: int = 256,
                  stream=None, keep_counts: bool = False, dense_threshold: float = float("inf"),
-                 dense_stream=None):
+                 dense_stream=None, dense_lanes: int = 1):
         from . import rdsplit as rd
         self.rd = rd
         self.dense_threshold = float(dense_threshold)
-        self.dense_stream = dense_stream
+        self.dense_lanes = max(1, int(dense_lanes))
+        # one CUDA stream per dense lane: the caller's dense_stream for the
+        # first lane (None: the legacy default stream), new streams for the others
+        self.dense_streams = [dense_stream]
+        if self.dense_lanes > 1:
+            import torch
+            self.dense_streams += [torch.cuda.Stream() for _ in range(self.dense_lanes - 1)]
         self.budget = float(budget_bytes)
         self.max_slots = int(max_slots)
         self.slice = int(slice_periods)
@@ -70,8 +78,9 @@ class Server:
         if stream is not None:
             rd.rdsplit_engine_set_stream(self.engine, stream)
         self.stream = stream
-        self.used = 0
+        self.used = 0              # device bytes held by admitted simulations (both lanes)
         self.active = {}
+        self._lock = threading.Lock()
 
     def close(self):
         if self.engine is not None:
@@ -84,101 +93,138 @@ class Server:
         except Exception:
             pass
 
-    def _admit(self, req, now: float, rec: Record):
-        w = req.workload() if callable(getattr(req, "workload", None)) else req.workload
-        nbytes = device_bytes(w.mesh.n_tets, w.model.n_species)
+    def _admit(self, rid: int, w, now: float, rec: Record, nbytes: int):
         sim = self.rd.Simulation(w.mesh, w.model, w.counts, stream=self.stream)
-        slot = self.rd.rdsplit_engine_add(self.engine, sim.h, w.t_end, w.seed)
-        tau = sim.tau
-        t, P = 0.0, 0
-        while t < w.t_end:
-            t = w.t_end if t + tau > w.t_end else t + tau
-            P += 1
+        try:
+            slot = self.rd.rdsplit_engine_add(self.engine, sim.h, w.t_end, w.seed)
+        except Exception:
+            sim.close()
+            raise
         rec.admitted = now
-        rec.tet_periods = w.mesh.n_tets * P
+        rec.tet_periods = w.mesh.n_tets * _periods(sim.tau, w.t_end)
         self.active[slot] = (rec, sim, nbytes)
-        self.used += nbytes
 
-    def _dense_worker(self, jobs, done, lock, t0, clock):
-        """Dense lane: run each large request alone, in arrival order."""
+    def _dense_worker(self, lane: int, jobs, done, t0, clock, errors):
+        """Dense lane: run each large request alone on this lane's stream, in
+        the order the lanes take them; its device memory was reserved at
+        admission and is released here."""
         rd = self.rd
+        stream = self.dense_streams[lane]
         while True:
             item = jobs.get()
             if item is None:
                 return
-            rec, w = item
-            rec.admitted = clock() - t0
-            with rd.Simulation(w.mesh, w.model, w.counts, stream=self.dense_stream) as sim:
-                tau = sim.tau
-                t, P = 0.0, 0
-                while t < w.t_end:
-                    t = w.t_end if t + tau > w.t_end else t + tau
-                    P += 1
-                rec.tet_periods = w.mesh.n_tets * P
-                sim.run(w.t_end, w.seed)
-                counts = sim.counts()
-            if self.keep_counts:
-                rec.counts = counts
-            rec.done = clock() - t0
-            with lock:
-                done.append(rec)
+            rec, w, nbytes = item
+            try:
+                rec.admitted = clock() - t0
+                with rd.Simulation(w.mesh, w.model, w.counts, stream=stream) as sim:
+                    rec.tet_periods = w.mesh.n_tets * _periods(sim.tau, w.t_end)
+                    sim.run(w.t_end, w.seed)
+                    counts = sim.counts()
+                if self.keep_counts:
+                    rec.counts = counts
+                rec.done = clock() - t0
+                with self._lock:
+                    done.append(rec)
+            except BaseException as e:   # reported by serve(), never dropped
+                with self._lock:
+                    errors.append((rec.rid, e))
+            finally:
+                with self._lock:
+                    self.used -= nbytes
+                    self._dense_out -= 1
 
     def serve(self, requests, prepared=None, clock=time.perf_counter):
         """Serve `requests` (objects with .rid, .arrival in seconds from the
         start, and .workload); `prepared` may map rid -> Workload built ahead
         of time (inputs arriving with the request).  Returns the records in
-        completion order."""
+        completion order.  Requests are admitted in arrival order while the
+        device budget (both lanes) and the engine's slots allow; an error in
+        either lane is raised here."""
         rd = self.rd
-        order = sorted(requests, key=lambda r: r.arrival)
-        pending = deque(order)
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
         waiting = deque()
         records = {}
         done = []
-        lock = threading.Lock()
+        errors = []
         jobs = queue.Queue()
+        self._dense_out = 0
         t0 = clock()
-        worker = None
+        workers = []
         if self.dense_threshold < float("inf"):
-            worker = threading.Thread(target=self._dense_worker, args=(jobs, done, lock, t0, clock), daemon=True)
-            worker.start()
-        while pending or waiting or self.active:
-            now = clock() - t0
-            while pending and pending[0].arrival <= now:
-                r = pending.popleft()
-                records[r.rid] = Record(r.rid, r.arrival)
-                w = prepared[r.rid] if prepared is not None else r.workload()
-                if w.mesh.n_tets * w.model.n_species >= self.dense_threshold:
-                    jobs.put((records[r.rid], w))
-                else:
+            for lane in range(self.dense_lanes):
+                th = threading.Thread(target=self._dense_worker, args=(lane, jobs, done, t0, clock, errors),
+                                      daemon=True)
+                th.start()
+                workers.append(th)
+        try:
+            while pending or waiting or self.active or self._dense_out > 0:
+                if errors:
+                    rid, e = errors[0]
+                    raise RuntimeError(f"request {rid} failed in the dense lane: {e}") from e
+                now = clock() - t0
+                while pending and pending[0].arrival <= now:
+                    r = pending.popleft()
+                    records[r.rid] = Record(r.rid, r.arrival)
                     waiting.append(r)
-            while waiting and len(self.active) < self.max_slots:
-                r = waiting[0]
-                w = prepared[r.rid] if prepared is not None else r.workload()
-                need = device_bytes(w.mesh.n_tets, w.model.n_species)
-                if self.used + need > self.budget and self.active:
-                    break
-                waiting.popleft()
-                self._admit(_Prepared(r.rid, w), clock() - t0, records[r.rid])
-            if self.active:
-                rd.rdsplit_engine_step(self.engine, self.slice)
-                for slot in rd.rdsplit_engine_poll(self.engine):
-                    rec, sim, nbytes = self.active.pop(slot)
-                    counts = sim.counts()          # the result goes back to the host
-                    if self.keep_counts:
-                        rec.counts = counts
-                    rec.done = clock() - t0
-                    sim.close()
-                    self.used -= nbytes
-                    with lock:
-                        done.append(rec)
-            elif pending:
-                wait = pending[0].arrival - (clock() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
-        if worker is not None:
-            jobs.put(None)
-            worker.join()
+                while waiting:
+                    r = waiting[0]
+                    w = prepared[r.rid] if prepared is not None else r.workload()
+                    need = device_bytes(w.mesh.n_tets, w.model.n_species)
+                    dense = workers and w.mesh.n_tets * w.model.n_species >= self.dense_threshold
+                    with self._lock:
+                        busy = bool(self.active) or self._dense_out > 0
+                        if self.used + need > self.budget and busy:
+                            break
+                        if not dense and len(self.active) >= self.max_slots:
+                            break
+                        self.used += need
+                        if dense:
+                            self._dense_out += 1
+                    waiting.popleft()
+                    if dense:
+                        jobs.put((records[r.rid], w, need))
+                    else:
+                        try:
+                            self._admit(r.rid, w, clock() - t0, records[r.rid], need)
+                        except Exception:
+                            with self._lock:
+                                self.used -= need
+                            raise
+                if self.active:
+                    rd.rdsplit_engine_step(self.engine, self.slice)
+                    for slot in rd.rdsplit_engine_poll(self.engine):
+                        rec, sim, nbytes = self.active.pop(slot)
+                        counts = sim.counts()          # the result goes back to the host
+                        if self.keep_counts:
+                            rec.counts = counts
+                        rec.done = clock() - t0
+                        sim.close()
+                        with self._lock:
+                            self.used -= nbytes
+                            done.append(rec)
+                else:
+                    wait = pending[0].arrival - (clock() - t0) if pending else 0.001
+                    if wait > 0:
+                        time.sleep(min(wait, 0.002))
+        finally:
+            for _ in workers:
+                jobs.put(None)
+            for th in workers:
+                th.join()
+        if errors:
+            rid, e = errors[0]
+            raise RuntimeError(f"request {rid} failed in the dense lane: {e}") from e
         return done
+
+
+def _periods(tau: float, t_end: float) -> int:
+    """Periods of Algorithm 1 from 0 to t_end (the last one shortened)."""
+    t, P = 0.0, 0
+    while t < t_end:
+        t = t_end if t + tau > t_end else t + tau
+        P += 1
+    return P
 
 
 @dataclass

@@ -44,7 +44,19 @@ def entries():
         if r.n <= 16 and reqs < 12:
             e[f"request_{r.rid}_n{r.n}_S{r.S}"] = ("request", {"rid": r.rid}, -1)
             reqs += 1
+    # larger serving requests, stratified over the mesh sizes up to n = 60
+    # and the species counts 1..8; eleven of them have n_tets * n_species
+    # >= 1e6 and run in the server's dense lane
+    for r in I.serving_requests(64):
+        if r.rid in LARGE_REQUESTS:
+            e[f"request_{r.rid}_n{r.n}_S{r.S}"] = ("request", {"rid": r.rid}, -1)
     return e
+
+
+# request ids of the serving generator's first 64 requests with stored runs
+# beyond the twelve smallest: n 17-25 (31, 29, 47, 59, 35), 26-35 (36, 40,
+# 41, 63), 36-45 (27, 19, 10, 0, 45, 6) and 46-60 (55, 57, 24, 49)
+LARGE_REQUESTS = (31, 29, 47, 59, 35, 36, 40, 41, 63, 27, 19, 10, 0, 45, 6, 55, 57, 24, 49)
 
 
 def build_workload(kind, args):
@@ -82,8 +94,17 @@ def main(names):
     data = {}
     if os.path.exists(OUT):
         data = json.load(open(OUT))
-    # longest first
-    order = sorted(todo.items(), key=lambda kv: 0 if kv[1][0] == "bar" and kv[1][2] < 0 else 1)
+    # longest first (roughly: the full bar, then requests by size)
+    def cost(kv):
+        kind, args, maxp = kv[1]
+        if kind == "bar" and maxp < 0:
+            return -1e30
+        if kind == "request":
+            r = I.serving_requests(64)[args["rid"]]
+            return -float(r.n_tets * r.S * r.t_end)
+        return 0.0
+    from paper_1512_03126_gb300 import inputs as I
+    order = sorted(todo.items(), key=cost)
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(8, os.cpu_count() or 1)) as pool:
         for name, rec in pool.imap_unordered(run_entry, order):

@@ -1,5 +1,9 @@
 """Continuous-batching server: results equal the oracle's for each request
 alone, whatever the mix (tolerance 0)."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -32,3 +36,45 @@ def test_served_results_equal_each_request_alone(oracle):
         o, _, _ = oracle.run(w.mesh, w.model, w.counts, w.t_end, w.seed)
         assert np.array_equal(rec.counts, o), rec.rid
         assert rec.latency >= 0
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_runs.json")
+
+
+def _digest(c) -> str:
+    return hashlib.sha256(np.ascontiguousarray(c, dtype="<i4").tobytes()).hexdigest()
+
+
+def test_both_lanes_overlap_and_equal_the_oracle():
+    """Serving workload (Poisson-style staggered arrivals, n up to 59, 1-8
+    species, random chemistries): every stored request (n from 6 to 59, every
+    species count) served in one mix with a finite dense-lane threshold, so
+    that the large ones run on two dense lanes while the others run in the
+    batched engine, overlapping on the device.  Each result equals the
+    oracle's run of that request alone (stored SHA-256, tolerance 0)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1512_03126_gb300 import build
+    build.build()
+    from paper_1512_03126_gb300 import serving as SV
+    stored = {v["args"]["rid"]: v for k, v in json.load(open(GOLDEN)).items() if v["kind"] == "request"}
+    all_reqs = I.serving_requests(64)
+    reqs = [all_reqs[rid] for rid in sorted(stored)]
+    prepared = {r.rid: r.workload() for r in reqs}
+    threshold = 1e6
+    dense = {r.rid for r in reqs if r.n_tets * r.S >= threshold}
+    assert len(dense) >= 3 and len(dense) < len(reqs)
+    for k, r in enumerate(reqs):
+        r.arrival = 0.002 * k
+    srv = SV.Server(budget_bytes=150e9, max_slots=16, slice_periods=64, keep_counts=True,
+                    dense_threshold=threshold, dense_lanes=2)
+    try:
+        recs = srv.serve(reqs, prepared)
+    finally:
+        srv.close()
+    assert sorted(r.rid for r in recs) == sorted(stored)
+    for rec in recs:
+        assert _digest(rec.counts) == stored[rec.rid]["sha256"], rec.rid
+    # a dense-lane request ran while another request was on the device
+    iv = {r.rid: (r.admitted, r.done) for r in recs}
+    assert any(iv[d][0] < iv[o][1] and iv[o][0] < iv[d][1] for d in dense for o in iv if o != d)

@@ -73,7 +73,9 @@ def _server(fake, **kw):
     srv.used = 0
     srv.active = {}
     srv.dense_threshold = float("inf")
-    srv.dense_stream = None
+    srv.dense_lanes = kw.get("lanes", 1)
+    srv.dense_streams = [None] * srv.dense_lanes
+    srv._lock = SV.threading.Lock()
     return srv
 
 
@@ -138,8 +140,66 @@ def test_dense_lane_takes_large_requests():
     pairs = small + large
     srv = _server(fake, slots=4)
     srv.dense_threshold = 5_000
-    srv.dense_stream = None
     recs = srv.serve([p[0] for p in pairs], {p[0].rid: p[1] for p in pairs})
     assert sorted(Sim.ran) == [10, 11]
     assert sorted(fake.admitted_order) == [0, 1, 2]
     assert sorted(r.rid for r in recs) == [0, 1, 2, 10, 11]
+
+
+class _DenseSim(FakeRd.Simulation):
+    """A dense-lane simulation that records how many run at once."""
+    lock = SV.threading.Lock()
+    running = 0
+    peak = 0
+    fail_rid = None
+
+    def run(self, t_end, seed):
+        import time
+        with _DenseSim.lock:
+            _DenseSim.running += 1
+            _DenseSim.peak = max(_DenseSim.peak, _DenseSim.running)
+        time.sleep(0.02)
+        with _DenseSim.lock:
+            _DenseSim.running -= 1
+        if self.h.rid == _DenseSim.fail_rid:
+            raise RuntimeError("planted failure")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+
+def _dense_setup(budget_units, lanes, fail_rid=None):
+    fake = FakeRd(steps_to_finish=2)
+    fake.Simulation = _DenseSim
+    _DenseSim.running = _DenseSim.peak = 0
+    _DenseSim.fail_rid = fail_rid
+    pairs = [_req(i, 0.0, T=10_000) for i in range(4)]
+    one = SV.device_bytes(10_000, 1)
+    srv = _server(fake, slots=4, budget=budget_units * one, lanes=lanes)
+    srv.dense_threshold = 5_000
+    return srv, pairs
+
+
+def test_dense_lanes_share_the_memory_budget():
+    """Dense-lane requests reserve their device memory at admission: with room
+    for one at a time, two lanes never run two at once; with room for all,
+    both lanes overlap.  The budget is released when they finish."""
+    srv, pairs = _dense_setup(1.5, lanes=2)
+    recs = srv.serve([p[0] for p in pairs], {p[0].rid: p[1] for p in pairs})
+    assert sorted(r.rid for r in recs) == [0, 1, 2, 3]
+    assert _DenseSim.peak == 1 and srv.used == 0
+    srv, pairs = _dense_setup(10, lanes=2)
+    srv.serve([p[0] for p in pairs], {p[0].rid: p[1] for p in pairs})
+    assert _DenseSim.peak == 2 and srv.used == 0
+
+
+def test_dense_lane_error_is_raised():
+    """A failure in a dense lane is raised from serve(), not dropped."""
+    import pytest
+    srv, pairs = _dense_setup(10, lanes=2, fail_rid=2)
+    with pytest.raises(RuntimeError, match="request 2 failed"):
+        srv.serve([p[0] for p in pairs], {p[0].rid: p[1] for p in pairs})
+    assert srv.used == 0
