@@ -243,7 +243,7 @@ int rdsplit_engine_active(rdsplit_engine_t engine, int32_t* n_slots, int64_t* n_
 int rdsplit_engine_destroy(rdsplit_engine_t engine);
 /* Scheduling: `in_flight` simulations are processed at once (0 = as many
  * clusters as fit on the GPU at once; never more than that), each by a
- * thread-block cluster of `cluster` CTAs (1, 2 or 4; default 4) that share
+ * thread-block cluster of `cluster` CTAs (1, 2 or 4; default 2) that share
  * its work through distributed shared memory.  Fewer in flight keeps their
  * working sets in L2. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);

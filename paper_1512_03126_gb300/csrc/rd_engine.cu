@@ -613,7 +613,7 @@ struct rdsplit_engine {
     int32_t concurrency = 0;                  // simulations in flight (0 = as many as fit)
     int32_t last_in_flight = 0;               // clusters of the last launch
     int32_t last_max_active = 0;              // clusters that fit at once in the last launch
-    int32_t cluster = 4;                      // CTAs per simulation (1, 2 or 4)
+    int32_t cluster = 2;                      // CTAs per simulation (1, 2 or 4)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
     std::vector<int32_t> slot_q;              // local periods done
