@@ -72,6 +72,30 @@ def algorithmic_bytes_per_tet_period(S: int, R: int, masked: bool) -> int:
     return 16 + 56 * S + (8 if R > 0 else 0) + (4 if masked else 0)
 
 
+def host_cores() -> int:
+    """Cores this process may run on: the affinity mask, capped by a cgroup
+    (v2) CPU quota when one is set."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        quota, period = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if quota != "max":
+            n = max(1, min(n, int(int(quota) / int(period))))
+    except (OSError, ValueError):
+        pass
+    return n
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -148,6 +172,7 @@ def run_ours(args, rank, world, local_rank):
     T, S, R = w.mesh.n_tets, w.model.n_species, w.model.n_reactions
     stream = torch.cuda.current_stream()
     sim = rd.Simulation(w.mesh, w.model, stream=stream)
+    rd.rdsplit_set_period_kernel(sim.h, args.period_mode, args.period_block)
     from paper_1512_03126_gb300 import dist as D
     seed = D.rank_seed(w.seed, rank)
     d_init = torch.from_numpy(np.ascontiguousarray(w.counts)).to(dev)
@@ -197,7 +222,9 @@ def run_ours(args, rank, world, local_rank):
     per_launch_s = (kms / kn) / 1e3 if kn else float("nan")
     achieved = bpt * T / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    roofline = {"kernel": "k_period", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+    two, blk = rd.rdsplit_get_period_kernel(sim.h)
+    kname = f"k_period_light (block {blk}) + k_period_slow" if two else f"k_period (block {blk})"
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "bytes_per_tet_period": bpt, "launch_us": round(per_launch_s * 1e6, 3),
                 "sampled_launches": kn, "peak_source": f"{peak_kind} hbm_gbs"}
@@ -431,6 +458,9 @@ def run_ensemble(args, rank, world, local_rank):
     rd.rdsplit_engine_destroy(eng)
     for s in sims:
         s.close()
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = run_configs(args, stream, flush)
     serving = None
     if rank == 0 and not args.no_serving:
         serving = run_serving(args, stream)
@@ -450,7 +480,7 @@ def run_ensemble(args, rank, world, local_rank):
         "processed_entries_per_s": entries * args.steps * world / (total_ms / 1e3),
         "roofline": roofline, "tail": tail, "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
-        "serving": serving,
+        "serving": serving, "configs": configs,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
     }
 
@@ -490,6 +520,96 @@ def engine_tail(slot_times, periods, tets, in_flight: int) -> dict:
             "longest_sim_ms": float(span[i] / 1e6), "longest_sim_periods": int(P[i]),
             "longest_sim_tets": int(np.asarray(tets)[idx[i]]),
             "last_start_ms": float((st[:, 0].max() - t0) / 1e6)}
+
+
+# ----------------------------------------------------------------- configs --
+
+def time_dense(rd, w, steps: int, warmup: int, stream, flush, mode: int = 0, block: int = 0):
+    """One workload through rdsplit_run, from its initial state to t_end per
+    step: device time per step (CUDA events, L2 flushed between steps) and
+    the roofline of the period kernel from sampled launches."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sim = rd.Simulation(w.mesh, w.model, stream=stream)
+    rd.rdsplit_set_period_kernel(sim.h, mode, block)
+    d_init = torch.from_numpy(np.ascontiguousarray(w.counts)).to(dev)
+
+    def step():
+        rd.rdsplit_set_counts_device(sim.h, d_init)
+        rd.rdsplit_set_time(sim.h, 0.0, 0)
+        sim.run(w.t_end, w.seed)
+
+    for _ in range(warmup):
+        step()
+    _, periods = sim.time
+    T, S, R = w.mesh.n_tets, w.model.n_species, w.model.n_reactions
+    torch.cuda.synchronize()
+    l0 = rd.rdsplit_kernel_launches()
+    rd.rdsplit_set_timing(sim.h, 8)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    kms, kn = rd.rdsplit_get_timing(sim.h)
+    rd.rdsplit_set_timing(sim.h, 0)
+    launches = rd.rdsplit_kernel_launches() - l0
+    two, blk = rd.rdsplit_get_period_kernel(sim.h)
+    sim.close()
+    bpt = algorithmic_bytes_per_tet_period(S, R, w.model.mask is not None)
+    per_launch_s = (kms / kn) / 1e3 if kn else float("nan")
+    achieved = bpt * T / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    return {"value": T * periods * steps / (total / 1e3), "unit": UNIT, "ms_per_step": total / steps,
+            "steps": steps, "periods": periods, "n_tets": T, "species": S, "reactions": R,
+            "gpu_launches": launches,
+            "roofline": {"kernel": f"k_period_light (block {blk}) + k_period_slow" if two else f"k_period (block {blk})",
+                         "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_tet_period": bpt,
+                         "launch_us": round(per_launch_s * 1e6, 3), "sampled_launches": kn,
+                         "peak_source": f"{peak_kind} hbm_gbs"}}
+
+
+def oracle_one_core(w, seconds: float):
+    """The serial oracle, as it stands, on one host core: the first periods
+    of the workload (bounded to about `seconds`), as tet-period updates/s."""
+    from oracle import oracle as O
+    O.lib()
+    t0 = time.perf_counter()
+    O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=2)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, int(seconds / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    _, _, p = O.run(w.mesh, w.model, w.counts, w.t_end, w.seed, max_periods=n)
+    dt = time.perf_counter() - t0
+    return {"value": w.mesh.n_tets * p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {p} periods of {w.name}, one host core, {dt:.1f} s"}
+
+
+def run_configs(args, stream, flush):
+    """The single-mesh workloads through the dense period loop: the
+    3,072-tet diffusion cube, the 48,000-tet reaction-diffusion cube and the
+    2.4 M-tet bar, each with its roofline and a one-core oracle baseline."""
+    from paper_1512_03126_gb300 import inputs as I
+    from paper_1512_03126_gb300 import rdsplit as rd
+    out = {}
+    for name, make, steps in (("diffusion_cube_3072", I.config_diffusion_3072, 5),
+                              ("reaction_diffusion_cube_48000", I.config_reaction_diffusion_48k, 3),
+                              ("bar_20x20x1000", I.config_bar, 3)):
+        t0 = time.perf_counter()
+        w = make()
+        gen = time.perf_counter() - t0
+        r = time_dense(rd, w, steps, 2, stream, flush)
+        r["mesh_generation_s"] = round(gen, 1)
+        if not args.no_cpu_baseline:
+            r["cpu_baseline"] = oracle_one_core(w, args.config_cpu_seconds)
+        out[name] = r
+    return out
 
 
 # ----------------------------------------------------------------- serving --
@@ -661,6 +781,10 @@ def main():
     ap.add_argument("--max-slots", type=int, default=64, help="serving: simulations admitted at once")
     ap.add_argument("--dense-threshold", type=float, default=1e6,
                     help="serving: n_tets*n_species from which a request runs in the dense lane")
+    ap.add_argument("--period-mode", type=int, default=0, help="dense period kernel: 0 auto, 1 one pass, 2 two passes")
+    ap.add_argument("--period-block", type=int, default=0, help="dense period kernel: block size (0: by mesh size)")
+    ap.add_argument("--no-configs", action="store_true", help="skip the single-mesh workloads")
+    ap.add_argument("--config-cpu-seconds", type=float, default=5.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -174,6 +174,25 @@ int rdsplit_get_tau(rdsplit_mesh_t mesh, double* tau);
 /* Number of tets / species of the handle. */
 int rdsplit_get_shape(rdsplit_mesh_t mesh, int32_t* n_tets, int32_t* n_species);
 
+/*
+ * Kernel form of the period (Algorithm 1, Steps 2-3), a tuning choice with no
+ * effect on results (every draw is keyed by tet and period):
+ *   mode 1  one pass: gather, reactions and draws of each tet in one kernel
+ *   mode 2  two passes: a light pass runs the tets that need neither the
+ *           reaction phase nor the double-precision binomial (compiled
+ *           without those samplers, so it keeps more warps per SM) and
+ *           defers the others to a slow pass with the full step
+ *   mode 0  automatic (default): one pass
+ *   block   threads per block of the period kernel (of the light pass in
+ *           mode 2): a multiple of 32 in 32..256, or 0 (default) for a size
+ *           chosen from the mesh (smaller blocks for small meshes, so that
+ *           their tets spread over all SMs)
+ * rdsplit_get_period_kernel reports whether runs use two passes and the
+ * block size they use.
+ */
+int rdsplit_set_period_kernel(rdsplit_mesh_t mesh, int32_t mode, int32_t block);
+int rdsplit_get_period_kernel(rdsplit_mesh_t mesh, int32_t* two_passes, int32_t* block);
+
 /* Issue all of the handle's device work on `stream` (a cudaStream_t). */
 int rdsplit_set_stream(rdsplit_mesh_t mesh, void* stream);
 

@@ -142,8 +142,17 @@ int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) 
     if (std::isnan(t_end)) return fail(RDSPLIT_EINVAL, "rdsplit_run: t_end is NaN");
     DevMesh m = h->dev_mesh();
     DevState s = h->dev_state();
+    const bool split = two_pass(h);
+    const int block = period_block(h, sm_count());
+    if (split && h->t < t_end && max_periods != 0) {
+        cudaError_t ce = cudaMemsetAsync(h->dqn, 0, 2 * sizeof(int32_t), h->stream);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RDSPLIT_ECUDA, "rdsplit_run: %s", cudaGetErrorString(ce));
+        }
+    }
     int64_t j = 0;
-    const int4* prev = nullptr;
+    const int32_t* prev = nullptr;
     while (h->t < t_end && (max_periods < 0 || j < max_periods)) {
         if (h->period >= (int64_t)0xffffffffll)
             return fail(RDSPLIT_EOVERFLOW, "rdsplit_run: period index exceeds 2^32-1");
@@ -158,7 +167,7 @@ int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) 
             launch_thresholds(h->T, h->mp, h->g, h->G, tau_k, h->thr_last, h->stream);
             thr = h->thr_last;
         }
-        int4* cur = h->out[j & 1];
+        int32_t* cur = h->inbox[j & 1];
         PeriodArgs a{(uint32_t)h->period, tau_k, (float)tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->timing_stride > 0 && j % h->timing_stride == 0) {
@@ -166,7 +175,8 @@ int run_loop(rdsplit_mesh* h, double t_end, int64_t max_periods, uint64_t seed) 
             e1 = next_event(h);
         }
         if (e0 && e1) cudaEventRecord(e0, h->stream);
-        launch_period(m, h->mp, s, a, h->stream);
+        if (split) launch_period_split(m, h->mp, s, a, h->dq, h->dqn, (int32_t)(j & 1), block, h->stream);
+        else launch_period(m, h->mp, s, a, block, h->stream);
         if (e0 && e1) cudaEventRecord(e1, h->stream);
         prev = cur;
         h->t = last ? t_end : h->t + h->tau;
@@ -399,9 +409,11 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
     int rc;
     if ((rc = alloc_into(&h->D, (size_t)S, "D")) || (rc = alloc_into(&h->d_tau, 1, "tau")) ||
         (rc = alloc_into(&h->cnt, T * S, "counts")) || (rc = alloc_into(&h->rem, T * S, "remainders")) ||
-        (rc = alloc_into(&h->out[0], T * S, "out-slots")) || (rc = alloc_into(&h->out[1], T * S, "out-slots")) ||
+        (rc = alloc_into(&h->inbox[0], T * 4 * inbox_stride(S), "inboxes")) ||
+        (rc = alloc_into(&h->inbox[1], T * 4 * inbox_stride(S), "inboxes")) ||
         (rc = alloc_into(&h->thr, T * S, "thresholds")) || (rc = alloc_into(&h->thr_last, T * S, "thresholds")) ||
-        (rc = alloc_into(&h->staging, T * S, "staging")) || (rc = alloc_into(&h->avv, T, "avv"))) {
+        (rc = alloc_into(&h->staging, T * S, "staging")) || (rc = alloc_into(&h->avv, T, "avv")) ||
+        (rc = alloc_into(&h->dq, T, "deferred-tet queue")) || (rc = alloc_into(&h->dqn, 2, "queue counters"))) {
         h->free_model();
         return rc;
     }
@@ -428,6 +440,9 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
     launch_tau(h->D, S, h->gmax, tau_scale, h->d_tau, st);
     CUDA_TRY(cudaMemcpyAsync(&h->tau, h->d_tau, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemsetAsync(h->cnt, 0, T * S * sizeof(int32_t), st));
+    // boundary slots of the inboxes are never written and must read as zero
+    CUDA_TRY(cudaMemsetAsync(h->inbox[0], 0, T * 4 * inbox_stride(S) * sizeof(int32_t), st));
+    CUDA_TRY(cudaMemsetAsync(h->inbox[1], 0, T * 4 * inbox_stride(S) * sizeof(int32_t), st));
     CUDA_TRY(cudaMemsetAsync(h->rem, 0, T * S * sizeof(int32_t), st));
     CUDA_TRY(cudaStreamSynchronize(st));
     if (std::isfinite(h->tau)) launch_thresholds(h->T, mp, h->g, h->G, h->tau, h->thr, st);
@@ -522,6 +537,23 @@ int rdsplit_get_shape(rdsplit_mesh_t h, int32_t* n_tets, int32_t* n_species) {
 int rdsplit_set_stream(rdsplit_mesh_t h, void* stream) {
     if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_stream: NULL handle");
     h->stream = (cudaStream_t)stream;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_set_period_kernel(rdsplit_mesh_t h, int32_t mode, int32_t block) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_period_kernel: NULL handle");
+    if (mode < 0 || mode > 2) return fail(RDSPLIT_EINVAL, "rdsplit_set_period_kernel: mode must be 0, 1 or 2");
+    if (block != 0 && (block < 32 || block > 256 || block % 32))
+        return fail(RDSPLIT_EINVAL, "rdsplit_set_period_kernel: block must be 0 or a multiple of 32 in 32..256");
+    h->period_mode = mode;
+    h->period_block = block;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_get_period_kernel(rdsplit_mesh_t h, int32_t* two_passes, int32_t* block) {
+    if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_get_period_kernel: NULL handle");
+    if (two_passes) *two_passes = two_pass(h) ? 1 : 0;
+    if (block) *block = period_block(h, sm_count());
     return RDSPLIT_OK;
 }
 

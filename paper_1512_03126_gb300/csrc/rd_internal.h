@@ -49,8 +49,8 @@ constexpr int32_t kRuleMid = 2;
 void finish_model_params(ModelParams& mp);
 
 // Device arrays of one mesh + state.  Counts are species-major ([S][T]);
-// out-slots are [S][T][4]; src[t][f] = 4*adj[t][f] + (slot of t in that
-// neighbour) or -1.
+// inboxes are [T][4][Sp] (see PeriodArgs); src[t][f] = 4*adj[t][f] + (slot
+// of t in that neighbour) or -1.
 struct DevMesh {
     int32_t T;
     const int4* src;        // [T]
@@ -86,6 +86,14 @@ void launch_counts_out(int32_t T, int32_t S, const int32_t* st_major, int32_t* t
 
 // ---- one period (gather of the previous period fused with reactions and
 // diffusion of this one) and the closing gather --------------------------
+// Inboxes: int32 [T][4][Sp] with Sp = inbox_stride(S).  Slot [u][r] holds,
+// per species, the molecules that the neighbour across face r of tet u sent
+// to u in one period; a tet t writes its leavers through face f into slot
+// src[t].f = 4 u + r of its neighbour u (each interior slot has exactly one
+// writer per period, boundary slots are never written and stay zero), and
+// reads its own four slots, contiguous, in the next period.
+__host__ __device__ inline int32_t inbox_stride(int32_t S) { return S <= 2 ? S : (S + 3) & ~3; }
+
 struct PeriodArgs {
     uint32_t period;        // global period index (random-stream key)
     double tau_k;           // length of this period
@@ -93,14 +101,21 @@ struct PeriodArgs {
     uint64_t seed;
     int32_t first;          // 1: counts come from cnt (no pending transfer)
     const uint4* thr;       // [S][T] cumulative 32-bit face thresholds for tau_k
-    const int4* out_prev;   // [S][T] out-slots of the previous period
-    int4* out_cur;          // [S][T] out-slots written by this period
+    const int32_t* in_prev; // [T][4][Sp] inboxes filled by the previous period
+    int32_t* in_cur;        // [T][4][Sp] inboxes this period fills
 };
-void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a, int block,
                    cudaStream_t st);
-void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int4* out_last, cudaStream_t st);
+void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int32_t* in_last, cudaStream_t st);
+// The period in two passes (light pass, then the deferred tets): queue holds
+// T entries, qcount two counters (both zero before the first period of a
+// run; parity alternates 0, 1, 0, ... over the run's periods); `block` is the
+// light pass's block size (32..256, a multiple of 32).
+void launch_period_split(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+                         int32_t* queue, int32_t* qcount, int32_t parity, int block, cudaStream_t st);
 
 int64_t launches();
+int sm_count();       // multiprocessors of the current device
 void note_launch();   // count a launch issued outside this file's launchers
 
 }  // namespace rdk

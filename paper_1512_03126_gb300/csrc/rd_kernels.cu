@@ -10,11 +10,17 @@
 //   k_period       per tet: gather of the previous period's transfers, SSA
 //                  reactions with occupancy (Step 2), mean-corrected binomial
 //                  count and multinomial split (Step 3)
+//   k_period_light / k_period_slow
+//                  the same period in two passes for large meshes: the
+//                  common tets without the double-precision samplers, then
+//                  the deferred ones with them
 //   k_gather       the closing synchronous transfer of a run
 //
 // Layout: counts and remainders are species-major int32 [S][T] (coalesced);
-// out-slots are int4 [S][T] (one 16-byte store per tet and species, the four
-// faces of a tet in one sector so that neighbours reading them share it).
+// transfers go through inboxes int32 [T][4][Sp]: a tet writes what leaves
+// through face f into the neighbour's slot (a scattered store that nothing
+// waits for) and reads its own four slots, contiguous, in the next period
+// (a coalesced load), instead of gathering from its neighbours.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -238,6 +244,31 @@ void launch_avv(int32_t T, const double* vol, float2* avv, cudaStream_t st) {
     ++g_launches;
 }
 
+// A tet's counts at the start of a period: its molecules that stayed in the
+// previous period plus what its neighbours sent (its inbox), or the counts
+// of the handle in a run's first period.  Returns error bits.
+template <int SA>
+__device__ __forceinline__ uint32_t gather_counts(const DevState& s, const PeriodArgs& a, int t, int T, int S, int Sp,
+                                                  int32_t* N) {
+    uint32_t bad = 0;
+    int64_t n[SA];
+#pragma unroll
+    for (int sp = 0; sp < SA; ++sp) {
+        if (sp >= S) break;
+        n[sp] = a.first ? s.cnt[(int64_t)sp * T + t] : s.rem[(int64_t)sp * T + t];
+    }
+    if (!a.first) add_inbox<SA>(a.in_prev, t, S, Sp, n);
+#pragma unroll
+    for (int sp = 0; sp < SA; ++sp) {
+        if (sp >= S) break;
+        int64_t v = n[sp];
+        if (v > 2147483647) { bad |= kErrOverflow; v = 2147483647; }
+        if (v < 0) { bad |= kErrNegative; v = 0; }
+        N[sp] = (int32_t)v;
+    }
+    return bad;
+}
+
 // One period for one tet: apply the previous period's transfers, run the
 // reaction phase, draw the diffusion out-counts.  S_ > 0 fixes the species
 // count at compile time so that counts live in registers; S_ = 0 reads it
@@ -249,33 +280,22 @@ __global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, De
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = t < m.T;          // every lane stays for the warp draw
     const int T = m.T;
+    const int Sp = inbox_stride(S);
     int32_t N[SA];
     int4 o[SA];
+    int4 sr = make_int4(-1, -1, -1, -1);
     uint32_t bad = 0, heavy = 0;
     if (valid) {
-        int4 sr = m.src[t];
-#pragma unroll
-        for (int sp = 0; sp < SA; ++sp) {
-            if (sp >= S) break;
-            int64_t n;
-            if (a.first) {
-                n = s.cnt[(int64_t)sp * T + t];
-            } else {
-                n = (int64_t)s.rem[(int64_t)sp * T + t] +
-                    incoming(reinterpret_cast<const int32_t*>(a.out_prev + (int64_t)sp * T), sr);
-            }
-            if (n > 2147483647) { bad |= kErrOverflow; n = 2147483647; }
-            if (n < 0) { bad |= kErrNegative; n = 0; }
-            N[sp] = (int32_t)n;
-        }
+        sr = m.src[t];
+        bad |= gather_counts<SA>(s, a, t, T, S, Sp, N);
         bad |= step_tet<SA, kReact>(m, mp, a.period, a.tau_k, a.tau_kf, a.seed, a.thr, t, S, N, o, &heavy, s.err);
     }
     warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
     if (valid) {
+        push_inbox<SA>(a.in_cur, sr, S, Sp, o);
 #pragma unroll
         for (int sp = 0; sp < SA; ++sp) {
             if (sp >= S) break;
-            a.out_cur[(int64_t)sp * T + t] = o[sp];
             s.rem[(int64_t)sp * T + t] = N[sp];
         }
         if (bad) atomicOr(s.err, bad);
@@ -283,34 +303,176 @@ __global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, De
 }
 
 template <int S_>
-void launch_period_s(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+void launch_period_s(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a, int block,
                      cudaStream_t st) {
-    if (mp.any_reaction) k_period<S_, true><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
-    else k_period<S_, false><<<grid_for(m.T), kBlock, 0, st>>>(m, mp, s, a);
+    const int grid = (int)(((int64_t)m.T + block - 1) / block);
+    if (mp.any_reaction) k_period<S_, true><<<grid, block, 0, st>>>(m, mp, s, a);
+    else k_period<S_, false><<<grid, block, 0, st>>>(m, mp, s, a);
 }
 
-void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a, int block,
                    cudaStream_t st) {
     switch (mp.S) {
-        case 1: launch_period_s<1>(m, mp, s, a, st); break;
-        case 2: launch_period_s<2>(m, mp, s, a, st); break;
-        case 3: launch_period_s<3>(m, mp, s, a, st); break;
-        case 4: launch_period_s<4>(m, mp, s, a, st); break;
-        case 8: launch_period_s<8>(m, mp, s, a, st); break;
-        default: launch_period_s<0>(m, mp, s, a, st); break;
+        case 1: launch_period_s<1>(m, mp, s, a, block, st); break;
+        case 2: launch_period_s<2>(m, mp, s, a, block, st); break;
+        case 3: launch_period_s<3>(m, mp, s, a, block, st); break;
+        case 4: launch_period_s<4>(m, mp, s, a, block, st); break;
+        case 8: launch_period_s<8>(m, mp, s, a, block, st); break;
+        default: launch_period_s<0>(m, mp, s, a, block, st); break;
     }
     ++g_launches;
 }
 
-__global__ void k_gather(DevMesh m, int32_t S, DevState s, const int4* __restrict__ out_last) {
+// The same period split in two passes, for large meshes.  The light pass
+// runs every tet that needs neither the reaction phase (no reaction
+// possible, or one proved impossible by the single-precision test) nor the
+// double-precision binomial (all counts below kMoleculeCut): it is compiled
+// without the non-inlined samplers, so it holds fewer registers and more
+// warps per SM.  It defers every other tet to a queue, with its gathered
+// counts stored in rem; the slow pass runs the queued tets with the full
+// step.  Every draw is keyed by (tet, period), so the result equals the
+// fused kernel's.  queue holds T entries; qcount[parity] counts this
+// period's, and the light pass clears the other parity's for the next.
+template <int S_, bool kReact>
+__global__ void __launch_bounds__(kBlock, 3) k_period_light(DevMesh m, ModelParams mp, DevState s, PeriodArgs a,
+                                                            int32_t* __restrict__ queue, int32_t* qcount,
+                                                            int32_t parity) {
+    constexpr int SA = S_ > 0 ? S_ : kMaxS;
+    const int S = S_ > 0 ? S_ : mp.S;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < m.T;          // every lane stays for the warp draw
+    const int T = m.T;
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) qcount[parity ^ 1] = 0;
+    const int Sp = inbox_stride(S);
+    int32_t N[SA];
+    int4 o[SA];
+    int4 sr = make_int4(-1, -1, -1, -1);
+    uint32_t bad = 0, heavy = 0;
+    bool light = false;
+    if (valid) {
+        sr = m.src[t];
+        bad |= gather_counts<SA>(s, a, t, T, S, Sp, N);
+        light = step_is_light<SA, kReact>(m, mp, a.period, a.tau_kf, a.seed, t, S, N);
+        if (light) {
+            bad |= step_tet<SA, false, false>(m, mp, a.period, a.tau_k, a.tau_kf, a.seed, a.thr, t, S, N, o, &heavy,
+                                              s.err);
+        } else {
+#pragma unroll
+            for (int sp = 0; sp < SA; ++sp) {
+                if (sp >= S) break;
+                s.rem[(int64_t)sp * T + t] = N[sp];
+            }
+        }
+    }
+    // deferred tets: one queue slot reservation per warp
+    const unsigned dm = __ballot_sync(0xffffffffu, valid && !light);
+    if (dm) {
+        const int leader = __ffs(dm) - 1;
+        int at = 0;
+        if (lane == leader) at = atomicAdd(qcount + parity, __popc(dm));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (valid && !light) queue[at + __popc(dm & ((1u << lane) - 1u))] = t;
+    }
+    warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
+    if (valid && light) {
+        push_inbox<SA>(a.in_cur, sr, S, Sp, o);
+#pragma unroll
+        for (int sp = 0; sp < SA; ++sp) {
+            if (sp >= S) break;
+            s.rem[(int64_t)sp * T + t] = N[sp];
+        }
+    }
+    if (bad) atomicOr(s.err, bad);
+}
+
+// The queued tets of one period with the full step (reaction phase and the
+// double-precision samplers), warp by warp over the queue.
+template <int S_, bool kReact>
+__global__ void __launch_bounds__(kBlock) k_period_slow(DevMesh m, ModelParams mp, DevState s, PeriodArgs a,
+                                                        const int32_t* __restrict__ queue, const int32_t* qcount,
+                                                        int32_t parity) {
+    constexpr int SA = S_ > 0 ? S_ : kMaxS;
+    const int S = S_ > 0 ? S_ : mp.S;
+    const int T = m.T;
+    const int n = qcount[parity];
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < n; base += nw * 32) {
+        const bool live = base + lane < n;
+        const int t = live ? queue[base + lane] : 0;
+        int32_t N[SA];
+        int4 o[SA];
+        uint32_t bad = 0, heavy = 0;
+        if (live) {
+#pragma unroll
+            for (int sp = 0; sp < SA; ++sp) {
+                if (sp >= S) break;
+                N[sp] = s.rem[(int64_t)sp * T + t];
+            }
+            bad |= step_tet<SA, kReact>(m, mp, a.period, a.tau_k, a.tau_kf, a.seed, a.thr, t, S, N, o, &heavy, s.err);
+        }
+        warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
+        if (live) {
+            push_inbox<SA>(a.in_cur, m.src[t], S, inbox_stride(S), o);
+#pragma unroll
+            for (int sp = 0; sp < SA; ++sp) {
+                if (sp >= S) break;
+                s.rem[(int64_t)sp * T + t] = N[sp];
+            }
+        }
+        if (bad) atomicOr(s.err, bad);
+    }
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+template <int S_>
+void launch_split_s(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+                    int32_t* queue, int32_t* qcount, int32_t parity, int block, cudaStream_t st) {
+    const int grid = (int)(((int64_t)m.T + block - 1) / block);
+    const int grid_slow = std::min(grid_for(m.T), 2 * sm_count());
+    if (mp.any_reaction) {
+        k_period_light<S_, true><<<grid, block, 0, st>>>(m, mp, s, a, queue, qcount, parity);
+        k_period_slow<S_, true><<<grid_slow, kBlock, 0, st>>>(m, mp, s, a, queue, qcount, parity);
+    } else {
+        k_period_light<S_, false><<<grid, block, 0, st>>>(m, mp, s, a, queue, qcount, parity);
+        k_period_slow<S_, false><<<grid_slow, kBlock, 0, st>>>(m, mp, s, a, queue, qcount, parity);
+    }
+}
+
+void launch_period_split(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
+                         int32_t* queue, int32_t* qcount, int32_t parity, int block, cudaStream_t st) {
+    switch (mp.S) {
+        case 1: launch_split_s<1>(m, mp, s, a, queue, qcount, parity, block, st); break;
+        case 2: launch_split_s<2>(m, mp, s, a, queue, qcount, parity, block, st); break;
+        case 3: launch_split_s<3>(m, mp, s, a, queue, qcount, parity, block, st); break;
+        case 4: launch_split_s<4>(m, mp, s, a, queue, qcount, parity, block, st); break;
+        case 8: launch_split_s<8>(m, mp, s, a, queue, qcount, parity, block, st); break;
+        default: launch_split_s<0>(m, mp, s, a, queue, qcount, parity, block, st); break;
+    }
+    g_launches += 2;
+}
+
+__global__ void k_gather(DevMesh m, int32_t S, DevState s, const int32_t* __restrict__ in_last) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
     const int T = m.T;
-    int4 sr = m.src[t];
+    const int Sp = inbox_stride(S);
+    const int32_t* box = in_last + (int64_t)t * 4 * Sp;
     uint32_t bad = 0;
     for (int sp = 0; sp < S; ++sp) {
-        int64_t n = s.rem[(int64_t)sp * T + t] +
-                    incoming(reinterpret_cast<const int32_t*>(out_last + (int64_t)sp * T), sr);
+        int64_t n = s.rem[(int64_t)sp * T + t];
+        for (int f = 0; f < 4; ++f) n += box[f * Sp + sp];
         if (n > 2147483647) { bad |= kErrOverflow; n = 2147483647; }
         if (n < 0) { bad |= kErrNegative; n = 0; }
         s.cnt[(int64_t)sp * T + t] = (int32_t)n;
@@ -318,8 +480,8 @@ __global__ void k_gather(DevMesh m, int32_t S, DevState s, const int4* __restric
     if (bad) atomicOr(s.err, bad);
 }
 
-void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int4* out_last, cudaStream_t st) {
-    k_gather<<<grid_for(m.T), kBlock, 0, st>>>(m, S, s, out_last);
+void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int32_t* in_last, cudaStream_t st) {
+    k_gather<<<grid_for(m.T), kBlock, 0, st>>>(m, S, s, in_last);
     ++g_launches;
 }
 

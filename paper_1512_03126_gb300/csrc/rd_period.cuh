@@ -23,15 +23,71 @@ __device__ __forceinline__ double zeta_of(double tau_k, double D, double Gt) {
     return z > 1.0 ? 1.0 : z;
 }
 
-// Incoming molecules of species s for tet t: what each neighbour sent through
-// the shared face in the previous period.
-__device__ __forceinline__ int64_t incoming(const int32_t* __restrict__ op, int4 sr) {
-    int64_t n = 0;
-    if (sr.x >= 0) n += __ldg(op + sr.x);
-    if (sr.y >= 0) n += __ldg(op + sr.y);
-    if (sr.z >= 0) n += __ldg(op + sr.z);
-    if (sr.w >= 0) n += __ldg(op + sr.w);
-    return n;
+// Molecules that arrived in tet t during the previous period, added to n[s]
+// for every species: the sum of t's four inbox slots (Sp = inbox_stride(S)
+// ints each, 16-byte aligned as a whole), read with 16-byte loads.
+template <int SA>
+__device__ __forceinline__ void add_inbox(const int32_t* __restrict__ in, int64_t t, int S, int Sp, int64_t* n) {
+    const int4* p = reinterpret_cast<const int4*>(in + t * 4 * Sp);
+    if (SA == 1 || Sp == 1) {
+        const int4 v = __ldg(p);
+        n[0] += (int64_t)v.x + v.y + v.z + v.w;
+        return;
+    }
+    if (SA == 2 || Sp == 2) {
+        const int4 a = __ldg(p), b = __ldg(p + 1);
+        n[0] += (int64_t)a.x + a.z + b.x + b.z;
+        if (SA > 1) n[1] += (int64_t)a.y + a.w + b.y + b.w;
+        return;
+    }
+    const int q4 = Sp >> 2;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+#pragma unroll
+        for (int q = 0; q < (SA + 3) / 4; ++q) {
+            if (q >= q4) break;
+            const int4 v = __ldg(p + f * q4 + q);
+            const int vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int sp = 4 * q + k;
+                if (sp < SA && sp < S) n[sp < SA ? sp : 0] += vals[k];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int face_of(const int4& v, int f) {
+    return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
+}
+
+// Send tet t's leavers (o[s], per face) to its neighbours: through face f
+// into inbox slot src.f of the neighbour (species beyond S written as 0).
+template <int SA>
+__device__ __forceinline__ void push_inbox(int32_t* __restrict__ in, int4 sr, int S, int Sp, const int4* o) {
+    const int slot[4] = {sr.x, sr.y, sr.z, sr.w};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (slot[f] < 0) continue;
+        int32_t* d = in + (int64_t)slot[f] * Sp;
+        if (SA == 1 || Sp == 1) {
+            d[0] = face_of(o[0], f);
+        } else if (SA == 2 || Sp == 2) {
+            *reinterpret_cast<int2*>(d) = make_int2(face_of(o[0], f), SA > 1 ? face_of(o[SA > 1 ? 1 : 0], f) : 0);
+        } else {
+#pragma unroll
+            for (int q = 0; q < (SA + 3) / 4; ++q) {
+                if (4 * q >= Sp) break;
+                int v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int s = 4 * q + k;
+                    v[k] = (s < S && s < SA) ? face_of(o[s < SA ? s : 0], f) : 0;
+                }
+                *reinterpret_cast<int4*>(d + 4 * q) = make_int4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
 }
 
 // Reaction phase of one tet (Algorithm 1, Step 2 and 2.1): Gillespie's

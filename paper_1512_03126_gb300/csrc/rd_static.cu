@@ -72,8 +72,8 @@ Layout layout_for(size_t T, size_t S, bool masked) {
     L.mask = o; o = align256(o + (masked ? 4 * T : 0));
     L.cnt = o;  o = align256(o + 4 * T * S);
     L.rem = o;  o = align256(o + 4 * T * S);
-    L.out0 = o; o = align256(o + 16 * T * S);
-    L.out1 = o; o = align256(o + 16 * T * S);
+    L.out0 = o; o = align256(o + 16 * T * (size_t)inbox_stride((int32_t)S));
+    L.out1 = o; o = align256(o + 16 * T * (size_t)inbox_stride((int32_t)S));
     L.thr = o;  o = align256(o + 16 * T * S);
     L.total = o;
     return L;
@@ -185,11 +185,14 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     uint32_t* mask32 = d_rxn_tet_mask ? (uint32_t*)(base + L.mask) : nullptr;
     int32_t* cnt = (int32_t*)(base + L.cnt);
     int32_t* rem = (int32_t*)(base + L.rem);
-    int4* out[2] = {(int4*)(base + L.out0), (int4*)(base + L.out1)};
+    int32_t* out[2] = {(int32_t*)(base + L.out0), (int32_t*)(base + L.out1)};
     uint4* thr = (uint4*)(base + L.thr);
 
-    // The array keeps the previous call's contents: clear what must start at 0.
+    // The array keeps the previous call's contents: clear what must start at
+    // 0 (the control words, and both inboxes, whose boundary slots are never
+    // written).
     cudaError_t ce = cudaMemsetAsync(base, 0, 3 * 256, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(base + L.out0, 0, L.thr - L.out0, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return rdapi::fail(RDSPLIT_ECUDA, "%s: memset failed: %s", where, cudaGetErrorString(ce));
@@ -217,7 +220,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     double tn = *t;
     int64_t pk = *period;
     int64_t j = 0;
-    const int4* prev = nullptr;
+    const int32_t* prev = nullptr;
     while (tn < t_end) {
         if (pk >= (int64_t)0xffffffffll) return rdapi::fail(RDSPLIT_EOVERFLOW, "%s: period index exceeds 2^32-1", where);
         double tau_k = tau;
@@ -227,9 +230,9 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
             last = true;
         }
         if (last) launch_thresholds(n_tets, mp, g, G, tau_k, thr, st);
-        int4* cur = out[j & 1];
+        int32_t* cur = out[j & 1];
         PeriodArgs a{(uint32_t)pk, tau_k, (float)tau_k, seed, j == 0 ? 1 : 0, thr, prev, cur};
-        launch_period(m, mp, s, a, st);
+        launch_period(m, mp, s, a, 256, st);
         prev = cur;
         tn = last ? t_end : tn + tau;
         pk += 1;

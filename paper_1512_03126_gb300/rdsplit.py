@@ -53,6 +53,8 @@ def _declare(L):
         "rdsplit_mesh_destroy": ([vp], C.c_int),
         "rdsplit_set_allocator": ([vp, vp, vp], C.c_int),
         "rdsplit_set_timing": ([vp, i32], C.c_int),
+        "rdsplit_set_period_kernel": ([vp, i32, i32], C.c_int),
+        "rdsplit_get_period_kernel": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "rdsplit_static_scratch_bytes": ([i32, i32, i32], C.c_size_t),
         "rdsplit_engine_create": ([i32, i64, C.POINTER(vp)], C.c_int),
         "rdsplit_engine_set_stream": ([vp, vp], C.c_int),
@@ -205,6 +207,19 @@ def rdsplit_set_stream(h, stream):
 
 def rdsplit_mesh_destroy(h):
     _check(lib().rdsplit_mesh_destroy(h))
+
+
+def rdsplit_set_period_kernel(h, mode: int = 0, block: int = 0):
+    """mode 0 automatic, 1 one pass, 2 two passes (light + deferred); block
+    0 = chosen from the mesh size."""
+    _check(lib().rdsplit_set_period_kernel(h, int(mode), int(block)))
+
+
+def rdsplit_get_period_kernel(h):
+    """(1 if runs use two passes else 0, light-pass block size)."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(lib().rdsplit_get_period_kernel(h, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def rdsplit_set_timing(h, stride: int):

@@ -29,11 +29,12 @@ def rd():
     return rdsplit
 
 
-def gpu_run(rd, w, t_end=None, max_periods=None, tau_scale=None):
+def gpu_run(rd, w, t_end=None, max_periods=None, tau_scale=None, mode=0, block=0):
     model = w.model
     if tau_scale is not None:
         model.tau_scale = tau_scale
     with rd.Simulation(w.mesh, model, w.counts) as sim:
+        rd.rdsplit_set_period_kernel(sim.h, mode, block)
         if max_periods is not None:
             sim.run_periods(max_periods, w.seed)
         else:
@@ -80,21 +81,25 @@ def _small_cases():
     return cases
 
 
+@pytest.mark.parametrize("mode, block", [(0, 0), (1, 256), (1, 64), (2, 256), (2, 96)])
 @pytest.mark.parametrize("name", list(_small_cases().keys()))
-def test_small_workloads_bit_exact(rd, oracle, name):
+def test_small_workloads_bit_exact(rd, oracle, name, mode, block):
+    """One-pass and two-pass period kernels (any light-pass block size)
+    give the oracle's counts."""
     w = _small_cases()[name]
-    g, (tg, pg) = gpu_run(rd, w)
+    g, (tg, pg) = gpu_run(rd, w, mode=mode, block=block)
     o, (to, po) = oracle_run(oracle, w)
     assert pg == po and tg == to
     assert_same(g, o)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("rid", [1, 2, 5, 7, 8, 13])
-def test_random_chemistries_bit_exact(rd, oracle, rid):
+def test_random_chemistries_bit_exact(rd, oracle, rid, mode):
     req = I.serving_requests(64)[rid]
     w = req.workload()
     w.t_end = min(w.t_end, 3e-3)
-    g, _ = gpu_run(rd, w)
+    g, _ = gpu_run(rd, w, mode=mode)
     o, _ = oracle_run(oracle, w)
     assert_same(g, o)
 
@@ -135,9 +140,10 @@ def test_two_tets_and_empty_state(rd, oracle):
     assert np.all(g == 0)
 
 
-def test_reaction_diffusion_48k_prefix(rd, oracle):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_reaction_diffusion_48k_prefix(rd, oracle, mode):
     w = I.config_reaction_diffusion_48k()
-    g, (tg, pg) = gpu_run(rd, w, max_periods=120)
+    g, (tg, pg) = gpu_run(rd, w, max_periods=120, mode=mode)
     o, (to, po) = oracle_run(oracle, w, max_periods=120)
     assert pg == po == 120
     assert_same(g, o)
@@ -237,14 +243,21 @@ def _golden_workload(rec):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("name", sorted(_golden().keys()))
-def test_full_size_against_stored_oracle_runs(rd, name):
+def _golden_cases():
+    names = sorted(_golden().keys())
+    # the automatic kernel form (one pass), and two passes on the bar and the
+    # 48k-cube prefixes
+    return [(n, 0) for n in names] + [("bar_20x20x1000@20", 2), ("reaction_diffusion_cube_48000@300", 2)]
+
+
+@pytest.mark.parametrize("name, mode", _golden_cases())
+def test_full_size_against_stored_oracle_runs(rd, name, mode):
     """Full-size workloads against the SHA-256 of the oracle's final counts
     (written by tests/golden/make_golden.py from the oracle alone)."""
     rec = _golden()[name]
     w = _golden_workload(rec)
     mp = rec["max_periods"]
-    g, (t, p) = gpu_run(rd, w, max_periods=mp if mp >= 0 else None)
+    g, (t, p) = gpu_run(rd, w, max_periods=mp if mp >= 0 else None, mode=mode)
     assert p == rec["period"]
     assert [int(x) for x in g.sum(0)] == rec["totals"]
     assert hashlib.sha256(np.ascontiguousarray(g, dtype="<i4").tobytes()).hexdigest() == rec["sha256"]
