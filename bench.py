@@ -461,6 +461,9 @@ def run_ensemble(args, rank, world, local_rank):
     configs = None
     if rank == 0 and not args.no_configs:
         configs = run_configs(args, stream, flush)
+    reorder = None
+    if rank == 0 and not args.no_reorder:
+        reorder = run_reorder(args, stream, flush)
     serving = None
     if rank == 0 and not args.no_serving:
         serving = run_serving(args, stream)
@@ -480,7 +483,7 @@ def run_ensemble(args, rank, world, local_rank):
         "processed_entries_per_s": entries * args.steps * world / (total_ms / 1e3),
         "roofline": roofline, "tail": tail, "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
-        "serving": serving, "configs": configs,
+        "serving": serving, "configs": configs, "reorder": reorder,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
     }
 
@@ -520,6 +523,52 @@ def engine_tail(slot_times, periods, tets, in_flight: int) -> dict:
             "longest_sim_ms": float(span[i] / 1e6), "longest_sim_periods": int(P[i]),
             "longest_sim_tets": int(np.asarray(tets)[idx[i]]),
             "last_start_ms": float((st[:, 0].max() - t0) / 1e6)}
+
+
+def run_reorder(args, stream, flush):
+    """The batched engine on meshes numbered at random (as a generator
+    without locality would number them): a sub-ensemble of the workload,
+    stored in the caller's numbering, stored along the library's Morton
+    curve (RDSPLIT_REORDER_SFC), and, for reference, in the generator's own
+    Morton numbering.  Device time of one engine launch each."""
+    import torch
+    from paper_1512_03126_gb300 import inputs as I
+    from paper_1512_03126_gb300 import rdsplit as rd
+    sizes = I.ensemble_sizes()
+    idx = list(range(0, len(sizes), max(1, len(sizes) // args.reorder_instances)))[: args.reorder_instances]
+    base = [I.ensemble_instance(i, int(sizes[i]), args.reorder_t_end) for i in idx]
+    shuffled = []
+    for i, w in zip(idx, base):
+        m, _ = I.shuffle_mesh(w.mesh, 100 + i)
+        shuffled.append(I.Workload(w.name, m, w.model, I.point_source(m, 1, 0, 6000), w.t_end, w.seed))
+    out = {"instances": len(idx), "t_end_s": args.reorder_t_end}
+    for label, ws, reorder in (("generator_order_ms", base, False), ("shuffled_ms", shuffled, False),
+                               ("shuffled_reordered_ms", shuffled, True)):
+        sims = [rd.Simulation(w.mesh, w.model, w.counts, stream=stream, reorder=reorder) for w in ws]
+        eng = rd.rdsplit_engine_create(len(ws), sum(w.mesh.n_tets for w in ws))
+        rd.rdsplit_engine_set_stream(eng, stream)
+        ms = []
+        for rep in range(3):
+            for s, w in zip(sims, ws):
+                rd.rdsplit_set_counts(s.h, w.counts)
+                rd.rdsplit_set_time(s.h, 0.0, 0)
+                rd.rdsplit_engine_add(eng, s.h, w.t_end, w.seed)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rd.rdsplit_engine_step(eng, 1 << 40)
+            e1.record(stream)
+            e1.synchronize()
+            rd.rdsplit_engine_poll(eng, 1 << 16)
+            if rep:
+                ms.append(e0.elapsed_time(e1))
+        out[label] = sum(ms) / len(ms)
+        rd.rdsplit_engine_destroy(eng)
+        for x in sims:
+            x.close()
+    return out
 
 
 # ----------------------------------------------------------------- configs --
@@ -784,6 +833,9 @@ def main():
     ap.add_argument("--period-mode", type=int, default=0, help="dense period kernel: 0 auto, 1 one pass, 2 two passes")
     ap.add_argument("--period-block", type=int, default=0, help="dense period kernel: block size (0: by mesh size)")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-mesh workloads")
+    ap.add_argument("--no-reorder", action="store_true", help="skip the shuffled-numbering engine measurement")
+    ap.add_argument("--reorder-instances", type=int, default=64)
+    ap.add_argument("--reorder-t-end", type=float, default=0.02)
     ap.add_argument("--config-cpu-seconds", type=float, default=5.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

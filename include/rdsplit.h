@@ -68,7 +68,8 @@ const char* rdsplit_last_error(void);
  *   face_area      float64 [n_tets][4], m^2, >= 0
  *   centroid_dist  float64 [n_tets][4], m, distance between the centroids of
  *                  t and adj[t][f]; > 0 where adj >= 0, ignored elsewhere
- *   flags          0 (reserved)
+ *   flags          0 (RDSPLIT_REORDER_SFC needs the centroids: see
+ *                  rdsplit_mesh_create_ex)
  *   out            receives the handle
  * The face coefficient g = A / (V dist) and the reverse-face table are
  * computed on the device; validation runs there too and a malformed mesh
@@ -77,6 +78,29 @@ const char* rdsplit_last_error(void);
 int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol,
                         const double* face_area, const double* centroid_dist,
                         int32_t flags, rdsplit_mesh_t* out);
+
+/*
+ * Same, with the tet centroids, so that the library can store the tets in
+ * its own order.
+ *   centroid       float64 [n_tets][3], m (finite), or NULL without a
+ *                  reordering flag
+ *   flags          0, or RDSPLIT_REORDER_SFC: store the tets along a Morton
+ *                  (Z-order) curve of their centroids (the box of the
+ *                  centroids cut into 2^21 steps per axis, ties by tet id),
+ *                  so that the tets a warp handles together are neighbours
+ *                  in space whatever the caller's numbering
+ * The reordering is internal: every array the caller passes or reads stays
+ * in the caller's (canonical) tet order, and random streams stay keyed by
+ * canonical ids, so results do not depend on the flag.
+ */
+#define RDSPLIT_REORDER_SFC 1
+int rdsplit_mesh_create_ex(int32_t n_tets, const int32_t* adj, const double* vol,
+                           const double* face_area, const double* centroid_dist,
+                           const double* centroid, int32_t flags, rdsplit_mesh_t* out);
+
+/* The stored order: perm[i] (int32 [n_tets], host) = canonical id of the
+ * i-th stored tet (the identity without a reordering). */
+int rdsplit_get_order(rdsplit_mesh_t mesh, int32_t* perm);
 
 /*
  * Attach a chemistry (Sec. III.C: species with diffusion constants,

@@ -206,18 +206,94 @@ int rdsplit_set_allocator(rdsplit_alloc_fn a, rdsplit_free_fn f, void* ctx) {
     return RDSPLIT_OK;
 }
 
-int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol, const double* face_area,
-                        const double* centroid_dist, int32_t flags, rdsplit_mesh_t* out) {
-    if (!out) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: out is NULL");
+}  // extern "C"
+
+namespace {
+
+// Spread the low 21 bits of x so that bit b lands on bit 3b.
+uint64_t spread3(uint64_t x) {
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Order of the tets along a Morton (Z-order) curve of their centroids:
+// perm[i] = canonical id of the i-th tet on the curve (ties by id).  The box
+// of the centroids is cut into 2^21 steps per axis.  Returns false if a
+// centroid is not finite.
+bool morton_order(int32_t T, const double* c, std::vector<int32_t>& perm) {
+    double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+    for (int32_t t = 0; t < T; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const double x = c[3 * (size_t)t + k];
+            if (!std::isfinite(x)) return false;
+            lo[k] = std::min(lo[k], x);
+            hi[k] = std::max(hi[k], x);
+        }
+    std::vector<std::pair<uint64_t, int32_t>> key((size_t)T);
+    for (int32_t t = 0; t < T; ++t) {
+        uint64_t m = 0;
+        for (int k = 0; k < 3; ++k) {
+            const double span = hi[k] - lo[k];
+            double q = span > 0.0 ? (c[3 * (size_t)t + k] - lo[k]) / span * 2097151.0 : 0.0;
+            q = std::min(std::max(q, 0.0), 2097151.0);
+            m |= spread3((uint64_t)q) << k;
+        }
+        key[(size_t)t] = {m, t};
+    }
+    std::sort(key.begin(), key.end());
+    perm.resize((size_t)T);
+    for (int32_t i = 0; i < T; ++i) perm[(size_t)i] = key[(size_t)i].second;
+    return true;
+}
+
+int mesh_create_impl(const char* where, int32_t n_tets, const int32_t* adj, const double* vol,
+                     const double* face_area, const double* centroid_dist, const double* centroid, int32_t flags,
+                     rdsplit_mesh_t* out) {
+    if (!out) return fail(RDSPLIT_EINVAL, "%s: out is NULL", where);
     *out = nullptr;
-    if (n_tets <= 0) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: n_tets must be > 0 (got %d)", n_tets);
-    if (n_tets > (1 << 29)) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: n_tets too large");
-    if (!adj || !vol || !face_area || !centroid_dist)
-        return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: NULL array");
-    if (flags != 0) return fail(RDSPLIT_EINVAL, "rdsplit_mesh_create: unknown flags 0x%x", flags);
+    if (n_tets <= 0) return fail(RDSPLIT_EINVAL, "%s: n_tets must be > 0 (got %d)", where, n_tets);
+    if (n_tets > (1 << 29)) return fail(RDSPLIT_EINVAL, "%s: n_tets too large", where);
+    if (!adj || !vol || !face_area || !centroid_dist) return fail(RDSPLIT_EINVAL, "%s: NULL array", where);
+    if (flags & ~RDSPLIT_REORDER_SFC) return fail(RDSPLIT_EINVAL, "%s: unknown flags 0x%x", where, flags);
+    const bool reorder = (flags & RDSPLIT_REORDER_SFC) != 0;
+    if (reorder && !centroid)
+        return fail(RDSPLIT_EINVAL, "%s: RDSPLIT_REORDER_SFC needs the tet centroids (rdsplit_mesh_create_ex)", where);
+    const size_t T = (size_t)n_tets;
+    // stored order: canonical, or along the space-filling curve (the
+    // arrays are permuted here; adjacency values are renumbered, invalid
+    // ones passed through for the device-side validation to reject)
+    std::vector<int32_t> perm, adj2;
+    std::vector<double> vol2, area2, dist2;
+    if (reorder) {
+        if (!morton_order(n_tets, centroid, perm)) return fail(RDSPLIT_EINVAL, "%s: a centroid is not finite", where);
+        std::vector<int32_t> inv(T);
+        for (size_t i = 0; i < T; ++i) inv[(size_t)perm[i]] = (int32_t)i;
+        adj2.resize(4 * T);
+        vol2.resize(T);
+        area2.resize(4 * T);
+        dist2.resize(4 * T);
+        for (size_t i = 0; i < T; ++i) {
+            const size_t c = (size_t)perm[i];
+            vol2[i] = vol[c];
+            for (int f = 0; f < 4; ++f) {
+                const int32_t u = adj[4 * c + f];
+                adj2[4 * i + f] = (u >= 0 && u < n_tets) ? inv[(size_t)u] : u;
+                area2[4 * i + f] = face_area[4 * c + f];
+                dist2[4 * i + f] = centroid_dist[4 * c + f];
+            }
+        }
+        adj = adj2.data();
+        vol = vol2.data();
+        face_area = area2.data();
+        centroid_dist = dist2.data();
+    }
     rdsplit_mesh* h = new rdsplit_mesh();
     h->T = n_tets;
-    const size_t T = (size_t)n_tets;
     int32_t* d_adj = nullptr;
     double *d_area = nullptr, *d_dist = nullptr;
     int rc = RDSPLIT_OK;
@@ -232,7 +308,7 @@ int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol, c
         (rc = alloc_into(&d_dist, 4 * T, "dist")) || (rc = alloc_into(&h->vol, T, "vol")) ||
         (rc = alloc_into(&h->src, T, "src")) || (rc = alloc_into(&h->g, 4 * T, "g")) ||
         (rc = alloc_into(&h->G, T, "G")) || (rc = alloc_into(&h->gmax, 1, "gmax")) ||
-        (rc = alloc_into(&h->err, 1, "err")))
+        (rc = alloc_into(&h->err, 1, "err")) || (reorder && (rc = alloc_into(&h->perm, T, "order"))))
         return cleanup(rc);
     cudaStream_t st = h->stream;
     cudaError_t ce = cudaSuccess;
@@ -240,17 +316,45 @@ int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol, c
     ce = ce ? ce : cudaMemcpyAsync(h->vol, vol, 8 * T, cudaMemcpyHostToDevice, st);
     ce = ce ? ce : cudaMemcpyAsync(d_area, face_area, 32 * T, cudaMemcpyHostToDevice, st);
     ce = ce ? ce : cudaMemcpyAsync(d_dist, centroid_dist, 32 * T, cudaMemcpyHostToDevice, st);
+    if (reorder) ce = ce ? ce : cudaMemcpyAsync(h->perm, perm.data(), 4 * T, cudaMemcpyHostToDevice, st);
     ce = ce ? ce : cudaMemsetAsync(h->gmax, 0, sizeof(unsigned long long), st);
     ce = ce ? ce : cudaMemsetAsync(h->err, 0, sizeof(uint32_t), st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
-        return cleanup(fail(RDSPLIT_ECUDA, "rdsplit_mesh_create: copy failed: %s", cudaGetErrorString(ce)));
+        return cleanup(fail(RDSPLIT_ECUDA, "%s: copy failed: %s", where, cudaGetErrorString(ce)));
     }
     launch_mesh_setup(n_tets, d_adj, h->vol, d_area, d_dist, h->src, h->g, h->G, h->gmax, h->err, st);
-    if ((rc = launch_check("rdsplit_mesh_create"))) return cleanup(rc);
-    if ((rc = check_err(h, "rdsplit_mesh_create"))) return cleanup(rc);
+    if ((rc = launch_check(where))) return cleanup(rc);
+    // the host arrays above are released on return: finish the copies first
+    if ((rc = check_err(h, where))) return cleanup(rc);
     *out = h;
     return cleanup(RDSPLIT_OK);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rdsplit_mesh_create(int32_t n_tets, const int32_t* adj, const double* vol, const double* face_area,
+                        const double* centroid_dist, int32_t flags, rdsplit_mesh_t* out) {
+    return mesh_create_impl("rdsplit_mesh_create", n_tets, adj, vol, face_area, centroid_dist, nullptr, flags, out);
+}
+
+int rdsplit_mesh_create_ex(int32_t n_tets, const int32_t* adj, const double* vol, const double* face_area,
+                           const double* centroid_dist, const double* centroid, int32_t flags, rdsplit_mesh_t* out) {
+    return mesh_create_impl("rdsplit_mesh_create_ex", n_tets, adj, vol, face_area, centroid_dist, centroid, flags,
+                            out);
+}
+
+int rdsplit_get_order(rdsplit_mesh_t h, int32_t* perm) {
+    if (!h || !perm) return fail(RDSPLIT_EINVAL, "rdsplit_get_order: NULL argument");
+    if (!h->perm) {
+        for (int32_t t = 0; t < h->T; ++t) perm[t] = t;
+        return RDSPLIT_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(perm, h->perm, 4 * (size_t)h->T, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return RDSPLIT_OK;
 }
 
 int rdsplit_set_transfer_rule(rdsplit_mesh_t h, int32_t rule) {
@@ -426,7 +530,7 @@ int rdsplit_set_model(rdsplit_mesh_t h, int32_t S, const double* D, int32_t R, c
             return rc;
         }
         cudaError_t ce = cudaMemcpyAsync(d_m8, mask, (size_t)R * T, cudaMemcpyHostToDevice, st);
-        if (ce == cudaSuccess) launch_pack_mask(h->T, R, d_m8, h->mask, st);
+        if (ce == cudaSuccess) launch_pack_mask(h->T, R, d_m8, h->mask, h->perm, st);
         cudaError_t ce2 = cudaStreamSynchronize(st);
         dev_free(d_m8);
         if (ce != cudaSuccess || ce2 != cudaSuccess) {
@@ -467,7 +571,7 @@ static int set_counts_impl(rdsplit_mesh_t h, const int32_t* counts, bool device)
         CUDA_TRY(cudaMemcpyAsync(h->staging, counts, n * 4, cudaMemcpyHostToDevice, h->stream));
         srcp = h->staging;
     }
-    launch_counts_in(h->T, h->S, srcp, h->cnt, h->err, h->stream);
+    launch_counts_in(h->T, h->S, srcp, h->cnt, h->err, h->perm, h->stream);
     int rc = launch_check("rdsplit_set_counts");
     if (rc) return rc;
     return check_err(h, "rdsplit_set_counts");
@@ -481,7 +585,7 @@ static int get_counts_impl(rdsplit_mesh_t h, int32_t* out, bool device) {
     if (!h->has_model) return fail(RDSPLIT_ESTATE, "rdsplit_get_counts: no model attached");
     const size_t n = (size_t)h->T * h->S;
     int32_t* dst = device ? out : h->staging;
-    launch_counts_out(h->T, h->S, h->cnt, dst, h->stream);
+    launch_counts_out(h->T, h->S, h->cnt, dst, h->perm, h->stream);
     int rc = launch_check("rdsplit_get_counts");
     if (rc) return rc;
     if (!device) CUDA_TRY(cudaMemcpyAsync(out, h->staging, n * 4, cudaMemcpyDeviceToHost, h->stream));

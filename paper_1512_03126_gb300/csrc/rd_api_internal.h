@@ -26,6 +26,7 @@ struct rdsplit_mesh {
     float2* avv = nullptr;
     unsigned long long* gmax = nullptr;
     uint32_t* err = nullptr;
+    int32_t* perm = nullptr;   // [T] canonical id of each stored tet (space-filling-curve order), or null
     // model and state
     double* D = nullptr;
     double* d_tau = nullptr;
@@ -57,7 +58,7 @@ struct rdsplit_mesh {
     double t = 0.0;
     int64_t period = 0;
 
-    rdk::DevMesh dev_mesh() const { return rdk::DevMesh{T, src, g, G, vol, mask, avv}; }
+    rdk::DevMesh dev_mesh() const { return rdk::DevMesh{T, src, g, G, vol, mask, avv, perm}; }
     rdk::DevState dev_state() const { return rdk::DevState{cnt, rem, err}; }
 
     void free_model() {
@@ -71,7 +72,7 @@ struct rdsplit_mesh {
     ~rdsplit_mesh() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         free_model();
-        void* ps[] = {src, g, G, vol, gmax, err, bits[0], bits[1], packed, N2};
+        void* ps[] = {src, g, G, vol, gmax, err, bits[0], bits[1], packed, N2, perm};
         for (void* p : ps) rdapi::dev_free(p);
     }
 };

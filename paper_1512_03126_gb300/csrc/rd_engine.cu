@@ -262,7 +262,8 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
             st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
                                                  &heavy, err, v.tstride, v.use_packed, pre);
         }
-        warp_split<SA>(heavy, d.seed, v.period, t, v.thr, v.T, N, o, v.tstride, v.use_packed, pre);
+        warp_split<SA>(heavy, d.seed, v.period, t, live ? key_of(d.m, t) : 0, v.thr, v.T, N, o, v.tstride,
+                       v.use_packed, pre);
         if (light) st.bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
     };
 
@@ -381,7 +382,8 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
             bad |= step_tet<SA, kReact, true>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
                                               &heavy, err, v.tstride, v.use_packed, pre);
         }
-        warp_split<SA>(heavy, d.seed, v.period, t, v.thr, v.T, N, o, v.tstride, v.use_packed, pre);
+        warp_split<SA>(heavy, d.seed, v.period, t, live ? key_of(d.m, t) : 0, v.thr, v.T, N, o, v.tstride,
+                       v.use_packed, pre);
         if (live) bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
     }
     __syncwarp();   // the queue is refilled by the next light pass

@@ -59,7 +59,11 @@ struct DevMesh {
     const double* vol;      // [T]
     const uint32_t* mask;   // [T]   reaction-on bits, or null
     const float2* avv;      // [T]   (N_A V_L, 1/(N_A V_L)) in single precision, or null
+    const int32_t* perm;    // [T]   canonical id of each stored tet, or null (stored = canonical order)
 };
+
+// The canonical id of stored tet t, which keys its random streams.
+__device__ __forceinline__ int key_of(const DevMesh& m, int t) { return m.perm ? __ldg(m.perm + t) : t; }
 
 struct DevState {
     int32_t* cnt;           // [S][T] counts between runs
@@ -79,10 +83,13 @@ void launch_avv(int32_t T, const double* vol, float2* avv, cudaStream_t st);
 void launch_count_ge(int32_t T, const double* G, unsigned long long xbits, unsigned int* count, cudaStream_t st);
 void launch_zeta_hist(int32_t T, const double* G, double tau, double D, int32_t nbins, unsigned long long* counts,
                       double* sum, unsigned long long* maxbits, cudaStream_t st);
-void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, cudaStream_t st);
-void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* st_major, uint32_t* err,
+// perm: canonical id of each stored tet, or null (no reordering).
+void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, const int32_t* perm,
                       cudaStream_t st);
-void launch_counts_out(int32_t T, int32_t S, const int32_t* st_major, int32_t* ts, cudaStream_t st);
+void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* st_major, uint32_t* err,
+                      const int32_t* perm, cudaStream_t st);
+void launch_counts_out(int32_t T, int32_t S, const int32_t* st_major, int32_t* ts, const int32_t* perm,
+                       cudaStream_t st);
 
 // ---- one period (gather of the previous period fused with reactions and
 // diffusion of this one) and the closing gather --------------------------

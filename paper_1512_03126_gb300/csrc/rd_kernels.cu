@@ -174,44 +174,53 @@ void launch_thresholds(int32_t T, const ModelParams& mp, const double* g, const 
     ++g_launches;
 }
 
-__global__ void k_pack_mask(int32_t T, int32_t R, const uint8_t* __restrict__ m8, uint32_t* __restrict__ m32) {
+__global__ void k_pack_mask(int32_t T, int32_t R, const uint8_t* __restrict__ m8, uint32_t* __restrict__ m32,
+                            const int32_t* __restrict__ perm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
+    const int c = perm ? perm[t] : t;
     uint32_t bits = 0;
     for (int r = 0; r < R; ++r)
-        if (m8[(size_t)r * T + t]) bits |= 1u << r;
+        if (m8[(size_t)r * T + c]) bits |= 1u << r;
     m32[t] = bits;
 }
 
-void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, cudaStream_t st) {
-    k_pack_mask<<<grid_for(T), kBlock, 0, st>>>(T, R, mask8, mask32);
+void launch_pack_mask(int32_t T, int32_t R, const uint8_t* mask8, uint32_t* mask32, const int32_t* perm,
+                      cudaStream_t st) {
+    k_pack_mask<<<grid_for(T), kBlock, 0, st>>>(T, R, mask8, mask32, perm);
     ++g_launches;
 }
 
+// Counts between the caller's canonical [T][S] order and the stored [S][T]
+// (stored tet t is canonical tet perm[t], or t without a reordering).
 __global__ void k_counts_in(int32_t T, int32_t S, const int32_t* __restrict__ ts, int32_t* __restrict__ sm,
-                            uint32_t* err) {
+                            uint32_t* err, const int32_t* __restrict__ perm) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)T * S) return;
     int t = (int)(i / S), s = (int)(i - (int64_t)t * S);
-    int32_t v = ts[i];
+    const int64_t c = perm ? perm[t] : t;
+    int32_t v = ts[c * S + s];
     if (v < 0) { atomicOr(err, kErrNegative); v = 0; }
     sm[(int64_t)s * T + t] = v;
 }
 
-__global__ void k_counts_out(int32_t T, int32_t S, const int32_t* __restrict__ sm, int32_t* __restrict__ ts) {
+__global__ void k_counts_out(int32_t T, int32_t S, const int32_t* __restrict__ sm, int32_t* __restrict__ ts,
+                             const int32_t* __restrict__ perm) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)T * S) return;
     int t = (int)(i / S), s = (int)(i - (int64_t)t * S);
-    ts[i] = sm[(int64_t)s * T + t];
+    const int64_t c = perm ? perm[t] : t;
+    ts[c * S + s] = sm[(int64_t)s * T + t];
 }
 
-void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* sm, uint32_t* err, cudaStream_t st) {
-    k_counts_in<<<grid_for((int64_t)T * S), kBlock, 0, st>>>(T, S, ts, sm, err);
+void launch_counts_in(int32_t T, int32_t S, const int32_t* ts, int32_t* sm, uint32_t* err, const int32_t* perm,
+                      cudaStream_t st) {
+    k_counts_in<<<grid_for((int64_t)T * S), kBlock, 0, st>>>(T, S, ts, sm, err, perm);
     ++g_launches;
 }
 
-void launch_counts_out(int32_t T, int32_t S, const int32_t* sm, int32_t* ts, cudaStream_t st) {
-    k_counts_out<<<grid_for((int64_t)T * S), kBlock, 0, st>>>(T, S, sm, ts);
+void launch_counts_out(int32_t T, int32_t S, const int32_t* sm, int32_t* ts, const int32_t* perm, cudaStream_t st) {
+    k_counts_out<<<grid_for((int64_t)T * S), kBlock, 0, st>>>(T, S, sm, ts, perm);
     ++g_launches;
 }
 
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, De
         bad |= gather_counts<SA>(s, a, t, T, S, Sp, N);
         bad |= step_tet<SA, kReact>(m, mp, a.period, a.tau_k, a.tau_kf, a.seed, a.thr, t, S, N, o, &heavy, s.err);
     }
-    warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
+    warp_split<SA>(heavy, a.seed, a.period, t, valid ? key_of(m, t) : 0, a.thr, T, N, o);
     if (valid) {
         push_inbox<SA>(a.in_cur, sr, S, Sp, o);
 #pragma unroll
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_period_light(DevMesh m, ModelPara
         at = __shfl_sync(0xffffffffu, at, leader);
         if (valid && !light) queue[at + __popc(dm & ((1u << lane) - 1u))] = t;
     }
-    warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
+    warp_split<SA>(heavy, a.seed, a.period, t, valid ? key_of(m, t) : 0, a.thr, T, N, o);
     if (valid && light) {
         push_inbox<SA>(a.in_cur, sr, S, Sp, o);
 #pragma unroll
@@ -413,7 +422,7 @@ __global__ void __launch_bounds__(kBlock) k_period_slow(DevMesh m, ModelParams m
             }
             bad |= step_tet<SA, kReact>(m, mp, a.period, a.tau_k, a.tau_kf, a.seed, a.thr, t, S, N, o, &heavy, s.err);
         }
-        warp_split<SA>(heavy, a.seed, a.period, t, a.thr, T, N, o);
+        warp_split<SA>(heavy, a.seed, a.period, t, live ? key_of(m, t) : 0, a.thr, T, N, o);
         if (live) {
             push_inbox<SA>(a.in_cur, m.src[t], S, inbox_stride(S), o);
 #pragma unroll

@@ -99,7 +99,7 @@ __device__ __forceinline__ void push_inbox(int32_t* __restrict__ in, int4 sr, in
 // single-precision (N_A V, 1/(N_A V)) come in by value: a non-inlined
 // function that took the mesh by reference would pin the caller's copy of
 // it in local memory.
-static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint32_t period, double tau_k,
+static __device__ __noinline__ void react_tet(const ModelParams& mp, int key, uint32_t period, double tau_k,
                                               uint64_t seed, double vol_t, uint32_t on, float2 avf, int64_t* N,
                                               double* occ, double* tl, uint32_t& touched, int64_t* Nmid,
                                               uint32_t* err) {
@@ -117,7 +117,7 @@ static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint
         c[r] = ((on >> r) & 1u) ? (o == 0 ? kr * avv : (o == 1 ? kr : kr / avv)) : 0.0;
         if (c[r] > 0.0) cpos |= 1u << r;
     }
-    rdd::Stream st(seed, (uint32_t)t, period, rdd::kPurposeReaction, 0);
+    rdd::Stream st(seed, (uint32_t)key, period, rdd::kPurposeReaction, 0);
     double tc = 0.0;
     int events = 0;
     for (;;) {
@@ -207,7 +207,7 @@ static __device__ __noinline__ void react_tet(const ModelParams& mp, int t, uint
 // the half-step comparison rule N* is N(tau_k / 2) (Nmid); under the
 // first-order rule the caller passes touched = false, so N* = N(tau_k).
 static __device__ __noinline__ int4 diffuse(const double* __restrict__ G, const double* __restrict__ gface, int t,
-                                            int s, double Dsp, uint32_t period, double tau_k, uint64_t seed,
+                                            int key, int s, double Dsp, uint32_t period, double tau_k, uint64_t seed,
                                             int64_t Nt, bool touched, double occ, int64_t Nmid, int32_t rule,
                                             uint4 C) {
     int4 o = make_int4(0, 0, 0, 0);
@@ -218,14 +218,14 @@ static __device__ __noinline__ int4 diffuse(const double* __restrict__ G, const 
     if (touched && rule == kRuleMid) {
         Nstar = Nmid;                          // N(tau_k / 2), an integer: no rounding draw
     } else if (touched) {
-        rdd::Stream rs(seed, (uint32_t)t, period, rdd::kPurposeRounding, (uint32_t)s);
+        rdd::Stream rs(seed, (uint32_t)key, period, rdd::kPurposeRounding, (uint32_t)s);
         double nbar = occ / tau_k;
         double fl = floor(nbar);
         double frac = nbar - fl;
         Nstar = (int64_t)fl + (rs.u01() < frac ? 1 : 0);
     }
     if (Nstar <= 0) return o;
-    rdd::Stream ds(seed, (uint32_t)t, period, rdd::kPurposeDiffusion, (uint32_t)s);
+    rdd::Stream ds(seed, (uint32_t)key, period, rdd::kPurposeDiffusion, (uint32_t)s);
     if (Nstar < kMoleculeCut) {
         int64_t moved = 0;
         for (int64_t i = 0; i < Nstar; ++i) {
@@ -296,7 +296,7 @@ __device__ __forceinline__ float combos_f(const ModelParams& mp, int r, const in
 // exact path runs.
 template <int SA>
 __device__ __forceinline__ bool surely_no_event(const ModelParams& mp, const int32_t* N, uint32_t on, float2 av,
-                                                uint32_t period, float tau_kf, uint64_t seed, int t) {
+                                                uint32_t period, float tau_kf, uint64_t seed, int key) {
     float a0 = 0.0f;
     const int R = mp.R;
     for (int r = 0; r < R; ++r) {
@@ -307,7 +307,7 @@ __device__ __forceinline__ bool surely_no_event(const ModelParams& mp, const int
         float c = o == 0 ? mp.kf[r] * av.x : (o == 1 ? mp.kf[r] : mp.kf[r] * av.y);
         a0 += c * h;
     }
-    rdd::Stream st(seed, (uint32_t)t, period, rdd::kPurposeReaction, 0);
+    rdd::Stream st(seed, (uint32_t)key, period, rdd::kPurposeReaction, 0);
     uint64_t x = st.bits53();
     uint64_t y = 9007199254740991ull - x;     // (1 - u1) * 2^53
     uint32_t yhi = (uint32_t)(y >> 29);       // top 24 bits: yhi * 2^-24 <= 1 - u1
@@ -319,10 +319,10 @@ __device__ __forceinline__ bool surely_no_event(const ModelParams& mp, const int
 
 // One draw per molecule against the cumulative face thresholds (N* < 10 and
 // the count untouched by reactions, so N* = N).
-__device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, int t, int sp, int32_t n, uint4 C) {
+__device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, int key, int sp, int32_t n, uint4 C) {
     int4 o = make_int4(0, 0, 0, 0);
     if (C.w == 0u) return o;                 // nothing can leave (zeta * 2^32 < 1)
-    rdd::Stream ds(seed, (uint32_t)t, period, rdd::kPurposeDiffusion, (uint32_t)sp);
+    rdd::Stream ds(seed, (uint32_t)key, period, rdd::kPurposeDiffusion, (uint32_t)sp);
     for (int i = 0; i < n; ++i) {
         uint32_t u = ds.u32();
         if (rdd::below(u, C.x)) o.x += 1;
@@ -364,7 +364,7 @@ __device__ __forceinline__ bool step_is_light(const DevMesh& m, const ModelParam
     if (!kReact) return true;
     const uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
     if (!reaction_possible<SA>(mp, N, on)) return true;
-    return surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, t);
+    return surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, key_of(m, t));
 }
 
 // Steps 2 and 3 of one period for one tet, given its counts N after the
@@ -384,6 +384,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
                                              int thr_stride = 1, bool has_pre = false,
                                              uint4 pre = make_uint4(0u, 0u, 0u, 0u)) {
     const int64_t T = m.T;
+    const int key = key_of(m, t);
     uint32_t bad = 0;
     uint32_t touched = 0;
     double occ[SA];
@@ -391,7 +392,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
     if (kReact && kCalls) {
         uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
         const bool possible = reaction_possible<SA>(mp, N, on);
-        if (possible && !surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, t)) {
+        if (possible && !surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, key)) {
             int64_t N64[SA];
             double tl[SA];
 #pragma unroll
@@ -401,7 +402,7 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
                 occ[sp] = 0.0;
                 tl[sp] = 0.0;
             }
-            react_tet(mp, t, period, tau_k, seed, m.vol[t], mp.has_mask ? m.mask[t] : 0xffffffffu, m.avv[t], N64, occ,
+            react_tet(mp, key, period, tau_k, seed, m.vol[t], mp.has_mask ? m.mask[t] : 0xffffffffu, m.avv[t], N64, occ,
                       tl, touched, nmid, err);
 #pragma unroll
             for (int sp = 0; sp < SA; ++sp) {
@@ -422,13 +423,13 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
         bool tch = kReact && ((touched >> sp) & 1u) && mp.rule != kRuleEnd;
         if (Nt > 0) {
             if (!tch && Nt < kWarpSplitMin) {
-                x = split_molecules(seed, period, t, sp, Nt, (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
+                x = split_molecules(seed, period, key, sp, Nt, (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
             } else if (!tch && Nt < kMoleculeCut) {
                 *heavy |= 1u << sp;        // drawn by the whole warp (warp_split)
                 o[sp] = x;
                 continue;
             } else if (kCalls) {
-                x = diffuse(m.G, m.g, t, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
+                x = diffuse(m.G, m.g, t, key, sp, mp.D[sp], period, tau_k, seed, Nt, tch, tch ? occ[sp] : 0.0,
                             tch ? nmid[sp] : (int64_t)Nt, mp.rule,
                             (has_pre && sp == 0) ? pre : thr[(sp * T + t) * thr_stride]);
             }
@@ -441,13 +442,14 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
 
 
 // The per-molecule draw of one (tet, species) spread over a warp: lane l
-// computes Philox blocks l, l+32, ... of the tet's diffusion stream (block b
+// computes Philox blocks l, l+32, ... of the tet's diffusion stream (keyed
+// by the canonical id `key` of the stored tet t) (block b
 // holds the uniforms of molecules 4b..4b+3, exactly the words the sequential
 // draw would use) and the face counts are summed over the warp.  Every lane
 // of the warp must call this; lanes with heavy == 0 only help.  With has_pre,
 // `pre` holds the calling lane's species-0 thresholds, already loaded.
 template <int SA>
-__device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32_t period, int t,
+__device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32_t period, int t, int key,
                                            const uint4* __restrict__ thr, int64_t T, int32_t* N, int4* o,
                                            int thr_stride = 1, bool has_pre = false,
                                            uint4 pre = make_uint4(0u, 0u, 0u, 0u)) {
@@ -462,7 +464,7 @@ __device__ __forceinline__ void warp_split(uint32_t heavy, uint64_t seed, uint32
         if (lane == src) myC = (has_pre && my_sp == 0) ? pre : thr[(my_sp * T + t) * thr_stride];
         const int sp = __shfl_sync(kAll, my_sp, src);
         const int32_t n = __shfl_sync(kAll, pick<SA>(N, my_sp), src);
-        const int tt = __shfl_sync(kAll, t, src);
+        const int tt = __shfl_sync(kAll, key, src);
         const uint32_t pr = __shfl_sync(kAll, period, src);
         const uint32_t k0 = __shfl_sync(kAll, (uint32_t)seed, src);
         const uint32_t k1 = __shfl_sync(kAll, (uint32_t)(seed >> 32), src);

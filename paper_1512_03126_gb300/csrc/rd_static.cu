@@ -200,7 +200,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     launch_mesh_setup(n_tets, d_adj, d_vol, d_face_area, d_centroid_dist, src, g, G, gmax, err, st);
     k_static_tau<<<1, 32, 0, st>>>(mp, gmax, tau_scale, d_tau);
     note_launch();
-    if (mask32) launch_pack_mask(n_tets, n_reactions, d_rxn_tet_mask, mask32, st);
+    if (mask32) launch_pack_mask(n_tets, n_reactions, d_rxn_tet_mask, mask32, nullptr, st);
     launch_avv(n_tets, d_vol, avv, st);
     double tau = 0.0;
     ce = cudaMemcpyAsync(&tau, d_tau, sizeof tau, cudaMemcpyDeviceToHost, st);
@@ -210,9 +210,9 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
     }
     if ((rc = read_err(base, L, st, where))) return rc;
 
-    DevMesh m{n_tets, src, g, G, d_vol, mask32, avv};
+    DevMesh m{n_tets, src, g, G, d_vol, mask32, avv, nullptr};
     DevState s{cnt, rem, err};
-    launch_counts_in(n_tets, n_species, d_counts, cnt, err, st);
+    launch_counts_in(n_tets, n_species, d_counts, cnt, err, nullptr, st);
     if (std::isfinite(tau)) launch_thresholds(n_tets, mp, g, G, tau, thr, st);
 
     // Algorithm 1: Step 1 aligns the last period to t_end, Steps 2-3 run in
@@ -239,7 +239,7 @@ extern "C" int rdsplit_run_static(int32_t n_tets, const int32_t* d_adj, const do
         j += 1;
     }
     if (j > 0) launch_gather(m, n_species, s, prev, st);
-    launch_counts_out(n_tets, n_species, cnt, d_counts, st);
+    launch_counts_out(n_tets, n_species, cnt, d_counts, nullptr, st);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return rdapi::fail(RDSPLIT_ECUDA, "%s: launch failed: %s", where, cudaGetErrorString(ce));
     if ((rc = read_err(base, L, st, where))) return rc;

@@ -276,6 +276,20 @@ def triangle_sheet(nx: int, ny: int, size=(1e-6, 1e-6), jitter: float = 0.0, mes
                 dist=np.ascontiguousarray(dist), centroid=cen, shape=(nx, ny, 1), size=(Lx, Ly, 0.0))
 
 
+def shuffle_mesh(mesh: Mesh, seed: int) -> tuple:
+    """The same mesh with its tets renumbered by a seeded random permutation
+    (as a mesh generator without locality might number them).  Returns
+    (mesh, old_of_new): new tet i is old tet old_of_new[i]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    old = rng.permutation(mesh.n_tets)
+    new_of_old = np.empty_like(old)
+    new_of_old[old] = np.arange(mesh.n_tets)
+    adj = mesh.adj[old]
+    adj = np.where(adj >= 0, new_of_old[np.maximum(adj, 0)], -1).astype(np.int32)
+    return Mesh(adj=adj, vol=mesh.vol[old].copy(), area=mesh.area[old].copy(), dist=mesh.dist[old].copy(),
+                centroid=mesh.centroid[old].copy(), shape=mesh.shape, size=mesh.size), old
+
+
 def cube(n: int, L: float = 1e-6, jitter: float = 0.0, mesh_seed: int = 0) -> Mesh:
     return kuhn_box(n, n, n, (L, L, L), jitter, mesh_seed)
 

@@ -38,6 +38,8 @@ def _declare(L):
         "rdsplit_last_error": ([], C.c_char_p),
         "rdsplit_kernel_launches": ([], i64),
         "rdsplit_mesh_create": ([i32, vp, vp, vp, vp, i32, C.POINTER(vp)], C.c_int),
+        "rdsplit_mesh_create_ex": ([i32, vp, vp, vp, vp, vp, i32, C.POINTER(vp)], C.c_int),
+        "rdsplit_get_order": ([vp, vp], C.c_int),
         "rdsplit_set_model": ([vp, i32, vp, i32, vp, vp, vp, vp, dbl], C.c_int),
         "rdsplit_set_counts": ([vp, vp], C.c_int),
         "rdsplit_set_counts_device": ([vp, vp], C.c_int),
@@ -133,6 +135,28 @@ def rdsplit_mesh_create(n_tets, adj, vol, face_area, centroid_dist, flags=0):
     _check(lib().rdsplit_mesh_create(int(n_tets), _ptr(adj), _ptr(vol), _ptr(face_area),
                                      _ptr(centroid_dist), int(flags), C.byref(h)))
     return h
+
+
+RDSPLIT_REORDER_SFC = 1
+
+
+def rdsplit_mesh_create_ex(n_tets, adj, vol, face_area, centroid_dist, centroid=None, flags=0):
+    adj = _c(adj, np.int32, (n_tets, 4))
+    vol = _c(vol, np.float64, (n_tets,))
+    face_area = _c(face_area, np.float64, (n_tets, 4))
+    centroid_dist = _c(centroid_dist, np.float64, (n_tets, 4))
+    centroid = None if centroid is None else _c(centroid, np.float64, (n_tets, 3))
+    h = C.c_void_p()
+    _check(lib().rdsplit_mesh_create_ex(int(n_tets), _ptr(adj), _ptr(vol), _ptr(face_area), _ptr(centroid_dist),
+                                        _ptr(centroid), int(flags), C.byref(h)))
+    return h
+
+
+def rdsplit_get_order(h):
+    T, _ = rdsplit_get_shape(h)
+    out = np.empty(T, np.int32)
+    _check(lib().rdsplit_get_order(h, _ptr(out)))
+    return out
 
 
 def rdsplit_set_model(h, n_species, D, n_reactions, lhs, rhs, k, rxn_tet_mask=None, tau_scale=1.0):
@@ -399,8 +423,13 @@ class Simulation:
     """One mesh + model handle: ``Simulation(mesh, model)``, then
     ``set_counts``, ``run``, ``counts``."""
 
-    def __init__(self, mesh, model, counts=None, stream=None, rule: int = RDSPLIT_TRANSFER_MEAN):
-        self.h = rdsplit_mesh_create(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist)
+    def __init__(self, mesh, model, counts=None, stream=None, rule: int = RDSPLIT_TRANSFER_MEAN,
+                 reorder: bool = False):
+        if reorder:
+            self.h = rdsplit_mesh_create_ex(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist, mesh.centroid,
+                                            RDSPLIT_REORDER_SFC)
+        else:
+            self.h = rdsplit_mesh_create(mesh.n_tets, mesh.adj, mesh.vol, mesh.area, mesh.dist)
         try:
             rdsplit_set_model(self.h, model.n_species, model.D, model.n_reactions, model.lhs, model.rhs,
                               model.k, model.mask, model.tau_scale)
