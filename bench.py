@@ -344,6 +344,16 @@ def run_ensemble(args, rank, world, local_rank):
         rd.rdsplit_engine_step(eng, 1 << 40)
         rd.rdsplit_engine_poll(eng, 1 << 16)
 
+    # CTAs per simulation, chosen by timing one launch of each shape (untimed)
+    tuned = None
+    if not args.no_autotune:
+        from paper_1512_03126_gb300 import autotune
+        tuned = autotune.tune_engine(rd, sims, [w.t_end for w in ws], seeds, reset, stream, use_cache=False)
+        by = {r["cluster"]: r["ms"] for r in tuned["results"]}
+        tuned.update({"default_cluster": 2, "default_ms": by.get(2), "chosen_cluster": tuned["best"]["cluster"],
+                      "chosen_ms": by.get(tuned["best"]["cluster"])})
+        rd.rdsplit_engine_set_concurrency(eng, 0, tuned["best"]["cluster"])
+
     for _ in range(args.warmup):
         reset()
         batched()
@@ -481,7 +491,7 @@ def run_ensemble(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MiB write); per step the ensemble state is 2.3 GB",
                    "parallelism": f"replicas x{world} (each rank its own ensemble, own seeds)"},
         "processed_entries_per_s": entries * args.steps * world / (total_ms / 1e3),
-        "roofline": roofline, "tail": tail, "plain": plain,
+        "roofline": roofline, "tail": tail, "autotune": tuned, "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
         "serving": serving, "configs": configs, "reorder": reorder,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
@@ -653,7 +663,17 @@ def run_configs(args, stream, flush):
         t0 = time.perf_counter()
         w = make()
         gen = time.perf_counter() - t0
-        r = time_dense(rd, w, steps, 2, stream, flush)
+        default = time_dense(rd, w, steps, 2, stream, flush)
+        if args.no_autotune:
+            r = default
+        else:
+            from paper_1512_03126_gb300 import autotune
+            tuned = autotune.tune_period(rd, w, stream, use_cache=False)
+            best = tuned["best"]
+            r = time_dense(rd, w, steps, 2, stream, flush, best["mode"], best["block"])
+            r["autotune"] = {"chosen": best, "single_mesh": tuned["single_mesh"], "candidates": tuned["results"],
+                             "default": {"kernel": default["roofline"]["kernel"], "value": default["value"],
+                                         "ms_per_step": default["ms_per_step"]}}
         r["mesh_generation_s"] = round(gen, 1)
         if not args.no_cpu_baseline:
             r["cpu_baseline"] = oracle_one_core(w, args.config_cpu_seconds)
@@ -666,7 +686,8 @@ def run_configs(args, stream, flush):
 def run_serving(args, stream):
     """Continuous batching (Poisson arrivals at 200/s, requests drawn from the
     serving generator, 150 GB device budget): p50/p99 latency and throughput,
-    against the same requests run one after another through rdsplit_run."""
+    the offered load against the throughput reached, and the same requests
+    run one after another through rdsplit_run (serial plain)."""
     import torch
     from paper_1512_03126_gb300 import inputs as I, serving as SV
     from paper_1512_03126_gb300 import rdsplit as rd
@@ -679,14 +700,16 @@ def run_serving(args, stream):
     warm = SV.Server(150e9, 8, args.slice, stream=stream)
     warm.serve([type(r)(r.rid, 0.0, r.n, r.S, r.t_end, r.model_seed) for r in small], prepared)
     warm.close()
-    dense_stream = torch.cuda.Stream()
+    dense_stream = torch.cuda.Stream() if args.dense_threshold < float("inf") else None
     server = SV.Server(150e9, args.max_slots, args.slice, stream=stream, dense_threshold=args.dense_threshold,
-                       dense_stream=dense_stream)
+                       dense_stream=dense_stream, dense_lanes=args.dense_lanes, slice_work=args.slice_work)
     torch.cuda.synchronize()
     recs = server.serve(reqs, prepared)
     server.close()
     torch.cuda.synchronize()
     out = SV.summarize(recs)
+    arrival_span = max(r.arrival for r in reqs) - min(r.arrival for r in reqs)
+    offered = out["tet_periods"] / arrival_span if arrival_span > 0 else None
     # serial plain runs of the same requests
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -696,12 +719,16 @@ def run_serving(args, stream):
             sim.run(w.t_end, w.seed)
             sim.counts()
     serial_s = time.perf_counter() - t0
-    out.update({"unit": UNIT, "arrival_rate_per_s": 200.0, "budget_gb": 150, "slice_periods": args.slice,
-                "dense_lane_threshold_tet_species": args.dense_threshold,
+    out.update({"unit": UNIT, "arrival_rate_per_s": 200.0, "arrival_span_s": arrival_span,
+                "offered_load": offered,
+                "load_vs_throughput": (offered / out["throughput"]) if offered and out["throughput"] else None,
+                "saturated": bool(offered and out["throughput"] and offered > 1.2 * out["throughput"]),
+                "budget_gb": 150, "slice_periods": args.slice, "slice_work_tet_periods": args.slice_work,
+                "dense_lane_threshold_tet_species": args.dense_threshold, "dense_lanes": args.dense_lanes,
                 "max_slots": args.max_slots, "serial_plain_s": serial_s,
                 "serial_plain_throughput": out["tet_periods"] / serial_s,
                 "throughput_vs_serial_plain": (out["throughput"] * serial_s / out["tet_periods"]),
-                "request_generation_s": round(gen_s, 1),
+                "request_generation_s": round(gen_s, 1), "host_loop_s": server.host_s,
                 "latency": "completion - arrival, wall clock, including queueing, upload and read-back"})
     return out
 
@@ -825,14 +852,18 @@ def main():
     ap.add_argument("--ensemble-t-end", type=float, default=0.1, help="ensemble: simulated time per instance (s)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=400, help="serving: number of requests")
     ap.add_argument("--slice", type=int, default=256, help="serving: periods per engine launch")
-    ap.add_argument("--max-slots", type=int, default=64, help="serving: simulations admitted at once")
-    ap.add_argument("--dense-threshold", type=float, default=1e6,
-                    help="serving: n_tets*n_species from which a request runs in the dense lane")
+    ap.add_argument("--max-slots", type=int, default=128, help="serving: simulations admitted at once")
+    ap.add_argument("--slice-work", type=int, default=20_000_000,
+                    help="serving: tet-periods per simulation and engine launch (0: every one advances --slice)")
+    ap.add_argument("--dense-threshold", type=float, default=float("inf"),
+                    help="serving: n_tets*n_species from which a request runs in a dense lane (inf: none)")
+    ap.add_argument("--dense-lanes", type=int, default=2, help="serving: dense lanes")
     ap.add_argument("--period-mode", type=int, default=0, help="dense period kernel: 0 auto, 1 one pass, 2 two passes")
     ap.add_argument("--period-block", type=int, default=0, help="dense period kernel: block size (0: by mesh size)")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-mesh workloads")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-reorder", action="store_true", help="skip the shuffled-numbering engine measurement")
     ap.add_argument("--reorder-instances", type=int, default=64)
     ap.add_argument("--reorder-t-end", type=float, default=0.02)

@@ -290,6 +290,13 @@ int rdsplit_engine_destroy(rdsplit_engine_t engine);
  * its work through distributed shared memory.  Fewer in flight keeps their
  * working sets in L2. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
+/* Slices of equal cost: with max_tet_periods > 0, rdsplit_engine_step
+ * advances a simulation of T tets by min(n_steps, max(1, max_tet_periods /
+ * T)) periods, so that the largest simulations of a mix do not hold a
+ * launch while the clusters that ran the small ones idle (continuous
+ * batching).  0 (default) advances every simulation by n_steps.  Results
+ * do not depend on the slicing. */
+int rdsplit_engine_set_slice_work(rdsplit_engine_t engine, int64_t max_tet_periods);
 /* Profiling: time every engine launch with CUDA events (on != 0), and read
  * the periods advanced (maximum per step call, summed), the (simulation, tet)
  * entries processed, and the summed milliseconds / number of timed launches. */

@@ -199,9 +199,10 @@ struct PeriodView {
 };
 
 // The light pass of one period for one warp.  The bitmap is dealt to the
-// cluster's kW warps in runs of 8 words (256 tets, one 32-byte sector): run
-// r goes to warp r mod kW, so the active tets of a region are spread over
-// all warps.  A column is 4 runs of a warp (32 words, one per lane); a warp
+// cluster's kW warps in runs of 4 words (128 tets): run r goes to warp
+// r mod kW, so the active tets of a region are spread over all warps (runs
+// of 4 measured faster than runs of 1, 2 or 8).  A column is 8 runs of a
+// warp (32 words, one per lane); a warp
 // loads kGroup of its columns at once, clears them for their next use, and
 // appends the set bits of each column to its list in shared memory
 // (a prefix sum of the lanes' popcounts gives each lane its place); whenever
@@ -268,15 +269,15 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
     };
 
     // the word of lane `lane` in column kk of batch b: run j of this warp
-    // (8 words, one 32-byte sector), runs dealt round-robin over the warps
+    // (4 words), runs dealt round-robin over the warps
     auto word_of = [&](int b, int kk) {
-        const int j = (b * kGroup + kk) * 4 + (lane >> 3);
-        return (gw + j * kW) * 8 + (lane & 7);
+        const int j = (b * kGroup + kk) * 8 + (lane / 4);
+        return (gw + j * kW) * 4 + (lane % 4);
     };
     int b = st.g0;
     for (;; ++b) {
         if (!st.loaded) {
-            if ((gw + b * kGroup * 4 * kW) * 8 >= v.W) break;
+            if ((gw + b * kGroup * 8 * kW) * 4 >= v.W) break;
             uint32_t wds[kGroup];
 #pragma unroll
             for (int kk = 0; kk < kGroup; ++kk) {
@@ -615,6 +616,7 @@ struct rdsplit_engine {
     int32_t concurrency = 0;                  // simulations in flight (0 = as many as fit)
     int32_t last_in_flight = 0;               // clusters of the last launch
     int32_t last_max_active = 0;              // clusters that fit at once in the last launch
+    int64_t slice_work = 0;                   // tet-periods per simulation and step call (0: no limit)
     int32_t cluster = 2;                      // CTAs per simulation (1, 2 or 4)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
@@ -828,7 +830,12 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
         if (!h) continue;
         SlotDesc& d = e->h_desc[s];
         d.q0 = e->slot_q[s];
-        d.q1 = (int32_t)std::min<int64_t>((int64_t)d.P, (int64_t)d.q0 + n_steps);
+        // periods of this slice: n_steps, or fewer for a large simulation
+        // when a work budget per slice is set (tets x periods), so that the
+        // slices of one launch cost about the same
+        int64_t n = n_steps;
+        if (e->slice_work > 0) n = std::max<int64_t>(1, std::min<int64_t>(n_steps, e->slice_work / h->T));
+        d.q1 = (int32_t)std::min<int64_t>((int64_t)d.P, (int64_t)d.q0 + n);
         if (d.q1 <= d.q0) continue;
         items.push_back(s);
         work.push_back((double)(d.q1 - d.q0) * (double)h->T);
@@ -929,6 +936,12 @@ int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_
         return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_concurrency: bad argument");
     e->concurrency = in_flight;
     e->cluster = cluster;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_engine_set_slice_work(rdsplit_engine_t e, int64_t max_tet_periods) {
+    if (!e || max_tet_periods < 0) return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_slice_work: bad argument");
+    e->slice_work = max_tet_periods;
     return RDSPLIT_OK;
 }
 

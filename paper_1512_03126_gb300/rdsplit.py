@@ -74,6 +74,7 @@ def _declare(L):
         "rdsplit_engine_stats": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)], C.c_int),
         "rdsplit_engine_slot_times": ([vp, vp, i32], C.c_int),
         "rdsplit_engine_schedule": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "rdsplit_engine_set_slice_work": ([vp, i64], C.c_int),
         "rdsplit_run_static": ([i32, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, dbl, vp,
                                 C.POINTER(dbl), C.POINTER(i64), dbl, u64, vp], C.c_int),
         "rdsplit_get_timing": ([vp, C.POINTER(dbl), C.POINTER(i64)], C.c_int),
@@ -337,6 +338,10 @@ def rdsplit_engine_slot_times(e, n_slots: int):
     out = np.zeros((int(n_slots), 3), np.int64)
     _check(lib().rdsplit_engine_slot_times(e, _ptr(out), int(n_slots)))
     return out
+
+
+def rdsplit_engine_set_slice_work(e, max_tet_periods: int):
+    _check(lib().rdsplit_engine_set_slice_work(e, int(max_tet_periods)))
 
 
 def rdsplit_engine_schedule(e):

@@ -9,6 +9,10 @@ join at the next slice, finished ones leave and free their memory.  A
 request's latency is its completion time minus its arrival time (queueing,
 upload, simulation and read-back included).
 
+With `slice_work` > 0 a launch advances a large simulation by fewer periods
+(about slice_work / n_tets), so that the slices of one launch cost about
+the same and no cluster idles behind the largest request.
+
 Requests with n_tets * n_species at or above `dense_threshold` can instead
 go to a dense lane: `dense_lanes` worker threads, each running its requests
 one after another with rdsplit_run (every tet every period, the whole GPU)
@@ -59,7 +63,7 @@ class Server:
 
     def __init__(self, budget_bytes: float = 150e9, max_slots: int = 128, slice_periods: int = 256,
                  stream=None, keep_counts: bool = False, dense_threshold: float = float("inf"),
-                 dense_stream=None, dense_lanes: int = 1):
+                 dense_stream=None, dense_lanes: int = 1, slice_work: int = 0):
         from . import rdsplit as rd
         self.rd = rd
         self.dense_threshold = float(dense_threshold)
@@ -75,12 +79,15 @@ class Server:
         self.slice = int(slice_periods)
         self.keep_counts = keep_counts
         self.engine = rd.rdsplit_engine_create(self.max_slots, 2**31 - 1)
+        if slice_work:
+            rd.rdsplit_engine_set_slice_work(self.engine, int(slice_work))
         if stream is not None:
             rd.rdsplit_engine_set_stream(self.engine, stream)
         self.stream = stream
         self.used = 0              # device bytes held by admitted simulations (both lanes)
         self.active = {}
         self._lock = threading.Lock()
+        self.host_s = {"admit": 0.0, "step": 0.0, "retire": 0.0}   # wall time of the serving loop by phase
 
     def close(self):
         if self.engine is not None:
@@ -185,14 +192,19 @@ class Server:
                     if dense:
                         jobs.put((records[r.rid], w, need))
                     else:
+                        ta = clock()
                         try:
                             self._admit(r.rid, w, clock() - t0, records[r.rid], need)
                         except Exception:
                             with self._lock:
                                 self.used -= need
                             raise
+                        self.host_s["admit"] += clock() - ta
                 if self.active:
+                    ts = clock()
                     rd.rdsplit_engine_step(self.engine, self.slice)
+                    tr = clock()
+                    self.host_s["step"] += tr - ts
                     for slot in rd.rdsplit_engine_poll(self.engine):
                         rec, sim, nbytes = self.active.pop(slot)
                         counts = sim.counts()          # the result goes back to the host
@@ -203,6 +215,7 @@ class Server:
                         with self._lock:
                             self.used -= nbytes
                             done.append(rec)
+                    self.host_s["retire"] += clock() - tr
                 else:
                     wait = pending[0].arrival - (clock() - t0) if pending else 0.001
                     if wait > 0:

@@ -148,36 +148,70 @@ def test_every_cluster_shape_matches_oracle(rd, oracle_results, cluster, in_flig
             s.close()
 
 
-def test_full_size_ensemble_and_requests_in_one_launch(rd):
-    """Every stored full-size oracle run of an ensemble instance or a serving
-    request (tests/golden/oracle_runs.json, written from the oracle alone),
-    all advanced together by one persistent engine launch in the default
-    launch configuration, ends with the oracle's counts (SHA-256 of the final
-    counts, period index and per-species totals)."""
-    import hashlib
+def _stored_full_runs():
     import json
     import os
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_runs.json")
     recs = {k: v for k, v in json.load(open(path)).items()
             if v["kind"] in ("ensemble", "request") and v["max_periods"] < 0}
-    assert len(recs) >= 40
     ws, names = [], []
     for name, rec in sorted(recs.items()):
         a = rec["args"]
         ws.append(I.ensemble_instance(a["i"], a["n"]) if rec["kind"] == "ensemble"
                   else I.serving_requests(64)[a["rid"]].workload())
         names.append(name)
+    return recs, ws, names
+
+
+def _check_stored(recs, names, sims):
+    import hashlib
+    for name, s in zip(names, sims):
+        rec = recs[name]
+        g = s.counts()
+        t, p = s.time
+        assert p == rec["period"], name
+        assert [int(x) for x in g.sum(0)] == rec["totals"], name
+        assert hashlib.sha256(np.ascontiguousarray(g, dtype="<i4").tobytes()).hexdigest() == rec["sha256"], name
+
+
+def test_full_size_ensemble_and_requests_in_one_launch(rd):
+    """Every stored full-size oracle run of an ensemble instance or a serving
+    request (tests/golden/oracle_runs.json, written from the oracle alone),
+    all advanced together by one persistent engine launch in the default
+    launch configuration, ends with the oracle's counts (SHA-256 of the final
+    counts, period index and per-species totals)."""
+    recs, ws, names = _stored_full_runs()
+    assert len(recs) >= 60
     sims = [rd.Simulation(w.mesh, w.model, w.counts) for w in ws]
     try:
         rd.rdsplit_ensemble_run([s.h for s in sims], [w.t_end for w in ws], [w.seed for w in ws])
-        for name, w, s in zip(names, ws, sims):
-            rec = recs[name]
-            g = s.counts()
-            t, p = s.time
-            assert p == rec["period"], name
-            assert [int(x) for x in g.sum(0)] == rec["totals"], name
-            assert hashlib.sha256(np.ascontiguousarray(g, dtype="<i4").tobytes()).hexdigest() == rec["sha256"], name
+        _check_stored(recs, names, sims)
     finally:
+        for s in sims:
+            s.close()
+
+
+def test_full_size_in_equal_cost_slices(rd):
+    """The same stored runs advanced in many launches whose slices give each
+    simulation about the same work (rdsplit_engine_set_slice_work: large
+    meshes advance fewer periods per launch), as continuous batching does:
+    identical results."""
+    recs, ws, names = _stored_full_runs()
+    sims = [rd.Simulation(w.mesh, w.model, w.counts) for w in ws]
+    e = rd.rdsplit_engine_create(len(ws), sum(w.mesh.n_tets for w in ws))
+    try:
+        rd.rdsplit_engine_set_slice_work(e, 30_000_000)
+        for w, s in zip(ws, sims):
+            rd.rdsplit_engine_add(e, s.h, w.t_end, w.seed)
+        steps = 0
+        while rd.rdsplit_engine_active(e)[0] > 0:
+            rd.rdsplit_engine_step(e, 700)
+            rd.rdsplit_engine_poll(e)
+            steps += 1
+        assert steps > 10
+        _check_stored(recs, names, sims)
+    finally:
+        rd.rdsplit_engine_destroy(e)
         for s in sims:
             s.close()
 

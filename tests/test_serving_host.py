@@ -76,6 +76,7 @@ def _server(fake, **kw):
     srv.dense_lanes = kw.get("lanes", 1)
     srv.dense_streams = [None] * srv.dense_lanes
     srv._lock = SV.threading.Lock()
+    srv.host_s = {"admit": 0.0, "step": 0.0, "retire": 0.0}
     return srv
 
 
