@@ -217,6 +217,43 @@ int rdsplit_get_shape(rdsplit_mesh_t mesh, int32_t* n_tets, int32_t* n_species);
 int rdsplit_set_period_kernel(rdsplit_mesh_t mesh, int32_t mode, int32_t block);
 int rdsplit_get_period_kernel(rdsplit_mesh_t mesh, int32_t* two_passes, int32_t* block);
 
+/*
+ * Domain decomposition (Sec. III.D: each process advances its own tets to
+ * tau, buffers the changes for tets of other processes, and the buffers are
+ * exchanged and applied before the next period).  Each rank holds a handle
+ * of the whole mesh and advances only its range of tets; the molecules its
+ * tets send across cut faces land in inbox slots of tets it does not own,
+ * which the rank exports and the owner imports before its next period.
+ * Every draw is keyed by canonical tet ids, so the ranks together give the
+ * single-process result bit for bit.
+ *   rdsplit_partition_set    own tets [t0, t1) (not on a reordered mesh)
+ *   rdsplit_partition_step   one period of Algorithm 1 for the own tets,
+ *                            towards t_end exactly as rdsplit_run would take
+ *                            it (the last period shortened); the first step
+ *                            after set/end starts from the handle's counts;
+ *                            *more = 1 while t < t_end.  No period is run
+ *                            once t >= t_end.
+ *   rdsplit_inbox_export     after a step: d_buf (device, int32 [n][S]) =
+ *                            the molecules sent into inbox slots d_slots
+ *                            (device, int32 [n]; slot 4 u + r is face r of
+ *                            tet u) by this rank's tets
+ *   rdsplit_inbox_import     after a step, before the next: writes d_buf
+ *                            into the own tets' slots d_slots (what another
+ *                            rank's tets sent them)
+ *   rdsplit_partition_end    applies the last period's transfers to the own
+ *                            tets; their counts then read as after
+ *                            rdsplit_run (other tets' counts are not kept)
+ * The slot lists are the caller's: for ranks owning [a0, a1) and [b0, b1),
+ * the slots 4 u + r with u in [b0, b1) and adj[u][r] in [a0, a1), in
+ * increasing order, are exported by the first and imported by the second.
+ * Export and import synchronise the handle's stream before returning.
+ */
+int rdsplit_partition_set(rdsplit_mesh_t mesh, int32_t t0, int32_t t1);
+int rdsplit_partition_step(rdsplit_mesh_t mesh, double t_end, uint64_t seed, int32_t* more);
+int rdsplit_inbox_export(rdsplit_mesh_t mesh, const int32_t* d_slots, int32_t n, int32_t* d_buf);
+int rdsplit_inbox_import(rdsplit_mesh_t mesh, const int32_t* d_slots, int32_t n, const int32_t* d_buf);
+int rdsplit_partition_end(rdsplit_mesh_t mesh);
+
 /* Issue all of the handle's device work on `stream` (a cudaStream_t). */
 int rdsplit_set_stream(rdsplit_mesh_t mesh, void* stream);
 

@@ -644,6 +644,92 @@ int rdsplit_set_stream(rdsplit_mesh_t h, void* stream) {
     return RDSPLIT_OK;
 }
 
+int rdsplit_partition_set(rdsplit_mesh_t h, int32_t t0, int32_t t1) {
+    const char* where = "rdsplit_partition_set";
+    if (!h) return fail(RDSPLIT_EINVAL, "%s: NULL handle", where);
+    if (h->perm) return fail(RDSPLIT_EINVAL, "%s: not available on a reordered mesh", where);
+    if (t0 < 0 || t1 <= t0 || t1 > h->T) return fail(RDSPLIT_EINVAL, "%s: need 0 <= t0 < t1 <= n_tets", where);
+    h->part_lo = t0;
+    h->part_hi = t1;
+    h->part_j = 0;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_partition_step(rdsplit_mesh_t h, double t_end, uint64_t seed, int32_t* more) {
+    const char* where = "rdsplit_partition_step";
+    if (!h) return fail(RDSPLIT_EINVAL, "%s: NULL handle", where);
+    if (!h->has_model) return fail(RDSPLIT_ESTATE, "%s: no model attached", where);
+    if (std::isnan(t_end)) return fail(RDSPLIT_EINVAL, "%s: t_end is NaN", where);
+    if (h->part_hi <= h->part_lo) return fail(RDSPLIT_ESTATE, "%s: no partition set", where);
+    if (h->t < t_end) {
+        if (h->period >= (int64_t)0xffffffffll) return fail(RDSPLIT_EOVERFLOW, "%s: period index exceeds 2^32-1", where);
+        double tau_k = h->tau;
+        bool last = false;
+        if (h->t + h->tau > t_end) {
+            tau_k = t_end - h->t;
+            last = true;
+        }
+        const uint4* thr = h->thr;
+        if (last) {
+            launch_thresholds(h->T, h->mp, h->g, h->G, tau_k, h->thr_last, h->stream);
+            thr = h->thr_last;
+        }
+        const int64_t j = h->part_j;
+        if (j == 0 && two_pass(h)) {
+            CUDA_TRY(cudaMemsetAsync(h->dqn, 0, 2 * sizeof(int32_t), h->stream));
+        }
+        PeriodArgs a{(uint32_t)h->period, tau_k, (float)tau_k, seed, j == 0 ? 1 : 0, thr,
+                     h->inbox[(j + 1) & 1], h->inbox[j & 1], h->part_lo, h->part_hi};
+        const int block = period_block(h, sm_count());
+        if (two_pass(h)) launch_period_split(h->dev_mesh(), h->mp, h->dev_state(), a, h->dq, h->dqn, (int32_t)(j & 1),
+                                             block, h->stream);
+        else launch_period(h->dev_mesh(), h->mp, h->dev_state(), a, block, h->stream);
+        h->t = last ? t_end : h->t + h->tau;
+        h->period += 1;
+        h->part_j += 1;
+        int rc = launch_check(where);
+        if (rc) return rc;
+        if ((rc = check_err(h, where))) return rc;
+    }
+    if (more) *more = h->t < t_end ? 1 : 0;
+    return RDSPLIT_OK;
+}
+
+int rdsplit_partition_end(rdsplit_mesh_t h) {
+    const char* where = "rdsplit_partition_end";
+    if (!h) return fail(RDSPLIT_EINVAL, "%s: NULL handle", where);
+    if (h->part_j > 0) {
+        launch_gather(h->dev_mesh(), h->S, h->dev_state(), h->inbox[(h->part_j - 1) & 1], h->stream, h->part_lo,
+                      h->part_hi);
+        h->part_j = 0;
+        int rc = launch_check(where);
+        if (rc) return rc;
+    }
+    return check_err(h, where);
+}
+
+static int inbox_copy(rdsplit_mesh_t h, const int32_t* d_slots, int32_t n, int32_t* d_buf, bool out,
+                      const char* where) {
+    if (!h || (n > 0 && (!d_slots || !d_buf))) return fail(RDSPLIT_EINVAL, "%s: NULL argument", where);
+    if (n < 0) return fail(RDSPLIT_EINVAL, "%s: n < 0", where);
+    if (h->part_j == 0) return fail(RDSPLIT_ESTATE, "%s: no partition step since the last begin or end", where);
+    int32_t* box = h->inbox[(h->part_j - 1) & 1];
+    if (out) launch_inbox_export(h->S, box, d_slots, n, d_buf, h->stream);
+    else launch_inbox_import(h->S, box, d_slots, n, d_buf, h->stream);
+    int rc = launch_check(where);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return RDSPLIT_OK;
+}
+
+int rdsplit_inbox_export(rdsplit_mesh_t h, const int32_t* d_slots, int32_t n, int32_t* d_buf) {
+    return inbox_copy(h, d_slots, n, d_buf, true, "rdsplit_inbox_export");
+}
+
+int rdsplit_inbox_import(rdsplit_mesh_t h, const int32_t* d_slots, int32_t n, const int32_t* d_buf) {
+    return inbox_copy(h, d_slots, n, const_cast<int32_t*>(d_buf), false, "rdsplit_inbox_import");
+}
+
 int rdsplit_set_period_kernel(rdsplit_mesh_t h, int32_t mode, int32_t block) {
     if (!h) return fail(RDSPLIT_EINVAL, "rdsplit_set_period_kernel: NULL handle");
     if (mode < 0 || mode > 2) return fail(RDSPLIT_EINVAL, "rdsplit_set_period_kernel: mode must be 0, 1 or 2");

@@ -43,6 +43,8 @@ struct rdsplit_mesh {
     int32_t* dqn = nullptr;    // [2] deferred-tet counters by period parity
     int32_t period_mode = 0;   // 0 auto (one pass), 1 one pass (k_period), 2 two passes (light + slow)
     int32_t period_block = 0;  // threads per block of the period kernel (0: by mesh size)
+    int32_t part_lo = 0, part_hi = 0;  // partition steps advance stored tets [part_lo, part_hi)
+    int64_t part_j = 0;                // periods done since the partition run began
     rdk::ModelParams mp{};
     bool has_model = false;
     int32_t rule = 0;          // transfer rule, kept across rdsplit_set_model

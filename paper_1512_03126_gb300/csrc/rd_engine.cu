@@ -87,7 +87,9 @@ constexpr int kDynSmemBytes = kWarps * kListCap * 4;
 // Shared memory of the engine kernel, at file scope so that the period
 // functions below address it directly.
 __shared__ int32_t s_item;                          // work-item index (first CTA of the cluster)
-__shared__ uint32_t s_total[2];                     // molecule total of a reaction-free simulation; [1]: too large
+__shared__ unsigned long long s_mass[3];            // [0] molecules of the simulation (all species) at the
+                                                    // start of the period; [1], [2] net change by reactions
+                                                    // in periods of even / odd parity (two's complement)
 __shared__ uint32_t s_wbuf[kWarps][kGroup * 32];    // per warp: the bitmap words of its current batch
 __shared__ int32_t s_slowq[kWarps][kQueue];         // per warp: tets deferred to the rounds with the full step
 extern __shared__ int32_t s_list[];                 // [kWarps][kListCap]: per warp, active tets not yet run
@@ -110,7 +112,7 @@ struct LightState {
 template <int kC>
 struct PeriodView {
     int T, S, W, r, tstride;
-    bool use_packed, more, exact;
+    bool use_packed, more;
     double tau_k;
     float tau_kf;
     uint32_t period;
@@ -121,7 +123,7 @@ struct PeriodView {
     uint32_t* bnext;
     int64_t cstride;
 
-    __device__ __forceinline__ PeriodView(const SlotDesc& d, int q, bool exact_) {
+    __device__ __forceinline__ PeriodView(const SlotDesc& d, int q) {
         T = d.m.T;
         S = d.S;
         W = (T + 31) >> 5;
@@ -144,12 +146,15 @@ struct PeriodView {
         bcur = d.bits[r];
         bnext = d.bits[r ^ 1];
         more = q + 1 < d.q1;
-        exact = exact_;
     }
 
     // Transfer of one tet's molecules (kept and leaving) into the next
-    // counts, and its bits in the next bitmap (fire-and-forget ORs: a bit
-    // set twice is set once).
+    // counts (fire-and-forget integer adds), and its bits in the next bitmap
+    // (fire-and-forget ORs: a bit set twice is set once).  An add that takes
+    // a count past 2^31-1 wraps it negative; as the simulation's molecule
+    // total is kept below 2^32 (checked every period), the next read of the
+    // count, or the check at the end of the slice, sees it negative and
+    // reports the overflow, exactly when the dense gather would.
     template <int SA, bool kReact>
     __device__ __forceinline__ uint32_t scatter(const SlotDesc& d, const ModelParams& mp, int t, const int4& sr,
                                                 const int32_t* N, const int4* o) const {
@@ -162,12 +167,7 @@ struct PeriodView {
             if (s >= S) break;
             int32_t* Ns = Nnext + (int64_t)s * T * cstride;
             if (N[s] > 0) {
-                if (exact) {
-                    const int32_t old = atomicAdd(Ns + (int64_t)t * cstride, N[s]);
-                    if (old > 2147483647 - N[s]) bad |= kErrOverflow;
-                } else {
-                    red_add(Ns + (int64_t)t * cstride, N[s]);
-                }
+                red_add(Ns + (int64_t)t * cstride, N[s]);
                 keep = true;
             }
             const int ov[4] = {o[s].x, o[s].y, o[s].z, o[s].w};
@@ -175,13 +175,7 @@ struct PeriodView {
             for (int f = 0; f < 4; ++f) {
                 if (ov[f] <= 0) continue;
                 if (nbr[f] < 0) { bad |= kErrNegative; continue; }
-                int32_t* dst = Ns + (int64_t)(nbr[f] >> 2) * cstride;
-                if (exact) {
-                    const int32_t old = atomicAdd(dst, ov[f]);
-                    if (old > 2147483647 - ov[f]) bad |= kErrOverflow;
-                } else {
-                    red_add(dst, ov[f]);
-                }
+                red_add(Ns + (int64_t)(nbr[f] >> 2) * cstride, ov[f]);
                 send[f] = true;
             }
         }
@@ -214,12 +208,12 @@ struct PeriodView {
 // resume point, when the next round could overflow the queue.
 template <int SA, bool kReact, int kC>
 __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, const ModelParams* __restrict__ mpp,
-                                              int q, bool exact, uint32_t* err, LightState st) {
+                                              int q, uint32_t* err, LightState st) {
     constexpr unsigned kAll = 0xffffffffu;
     constexpr int kW = kC * kWarps;
     const SlotDesc& d = *dp;
     const ModelParams& mp = *mpp;
-    const PeriodView<kC> v(d, q, exact);
+    const PeriodView<kC> v(d, q);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int rank = kC > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
@@ -248,6 +242,10 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
             for (int s = 0; s < SA; ++s) {
                 if (s >= v.S) break;
                 N[s] = v.Ncur[((int64_t)s * v.T + t) * v.cstride];
+                if (N[s] < 0) {          // wrapped past 2^31-1 by the previous period's adds
+                    st.bad |= kErrOverflow;
+                    N[s] = 0;
+                }
             }
             light = step_is_light<SA, kReact>(d.m, mp, v.period, v.tau_kf, d.seed, t, v.S, N);
         }
@@ -355,10 +353,10 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
 // the full per-tet step: reactions and the non-inlined samplers.
 template <int SA, bool kReact, int kC>
 __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, const ModelParams* __restrict__ mpp, int q,
-                                           bool exact, uint32_t* err, int n) {
+                                           uint32_t* err, int n, unsigned long long* mass_delta) {
     const SlotDesc& d = *dp;
     const ModelParams& mp = *mpp;
-    const PeriodView<kC> v(d, q, exact);
+    const PeriodView<kC> v(d, q);
     const int lane = threadIdx.x & 31;
     const int32_t* slowq = s_slowq[threadIdx.x >> 5];
     uint32_t bad = 0;
@@ -370,6 +368,7 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
         int4 o[SA];
         int4 sr = make_int4(-1, -1, -1, -1);
         uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+        long long before = 0;
         if (live) {
             sr = d.packed ? *reinterpret_cast<const int4*>(d.packed + 2 * t) : d.m.src[t];
             if (v.use_packed) pre = d.packed[2 * t + 1];
@@ -379,6 +378,11 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
                 int32_t* p = v.Ncur + ((int64_t)s * v.T + t) * v.cstride;
                 N[s] = *p;
                 *p = 0;
+                if (N[s] < 0) {          // wrapped past 2^31-1 by the previous period's adds
+                    bad |= kErrOverflow;
+                    N[s] = 0;
+                }
+                before += N[s];
             }
             bad |= step_tet<SA, kReact, true>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
                                               &heavy, err, v.tstride, v.use_packed, pre);
@@ -386,6 +390,22 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
         warp_split<SA>(heavy, d.seed, v.period, t, live ? key_of(d.m, t) : 0, v.thr, v.T, N, o, v.tstride,
                        v.use_packed, pre);
         if (live) bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
+        if (kReact) {
+            // net molecules made by this tet's reactions: all it keeps and
+            // sends minus what it held
+            long long delta = 0;
+            if (live) {
+                delta = -before;
+#pragma unroll
+                for (int s = 0; s < SA; ++s) {
+                    if (s >= v.S) break;
+                    delta += (long long)N[s] + o[s].x + o[s].y + o[s].z + o[s].w;
+                }
+            }
+#pragma unroll
+            for (int dd = 16; dd > 0; dd >>= 1) delta += __shfl_xor_sync(0xffffffffu, delta, dd);
+            if (lane == 0 && delta != 0) atomicAdd(mass_delta, (unsigned long long)delta);
+        }
     }
     __syncwarp();   // the queue is refilled by the next light pass
     return bad;
@@ -402,9 +422,11 @@ __device__ __noinline__ uint32_t slow_pass(const SlotDesc* __restrict__ dp, cons
 // idempotent, so no membership test and no list are needed).  At the end of
 // a slice both bitmaps are zero.
 //
-// Count adds return the old value to detect a count above 2^31-1, except in
-// a simulation without reactions whose molecules sum to at most 2^31-1: no
-// count can overflow there, and the adds need not wait for a reply.
+// Count adds are fire-and-forget reductions.  A count that an add takes past
+// 2^31-1 wraps negative and is reported when read (next period, or the check
+// at the end of the slice); the molecule total of the simulation, tracked per
+// period (the slow pass adds what reactions make or consume), is kept below
+// 2^32 - 1 so that no count can wrap all the way round unseen.
 template <int SA, bool kReact, int kC>
 __global__ void __launch_bounds__(kRunBlock, 1)
 k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__ mps, const int32_t* __restrict__ order,
@@ -415,7 +437,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = kC > 1 ? (int)cluster.block_rank() : 0;
     int32_t* item = kC > 1 ? cluster.map_shared_rank(&s_item, 0) : &s_item;
-    uint32_t* total = kC > 1 ? cluster.map_shared_rank(&s_total[0], 0) : &s_total[0];
+    unsigned long long* mass = kC > 1 ? cluster.map_shared_rank(&s_mass[0], 0) : &s_mass[0];
     auto csync = [&]() {
         if (kC > 1) cluster.sync();
         else __syncthreads();
@@ -426,8 +448,7 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         csync();
         if (rank == 0 && threadIdx.x == 0) {
             *item = atomicAdd(head, 1);
-            total[0] = 0u;
-            total[1] = 0u;
+            mass[0] = mass[1] = mass[2] = 0ull;
         }
         csync();
         const int32_t k = *item;
@@ -447,11 +468,10 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
         const int S = d.S;
         const int W = (T + 31) >> 5;
         const bool inter = d.N2 != nullptr;   // one species, interleaved counts
-        const bool conserved = mp.R == 0;     // molecules are only moved
         uint32_t bad = 0;
         // initial bitmap: occupied tets and tets with a zero-order reaction on
         // (whole words, written by the first lane of each 32-tet run); and the
-        // molecule total of a reaction-free simulation
+        // simulation's molecule total
         unsigned long long mine = 0;
         for (int base = rank * kRunBlock; base < W * 32; base += kC * kRunBlock) {
             const int t = base + threadIdx.x;
@@ -462,43 +482,57 @@ k_engine_run(const SlotDesc* __restrict__ descs, const ModelParams* __restrict__
                     const int32_t c = d.N[0][(int64_t)s * T + t];
                     occ = occ || c > 0;
                     mine += (uint32_t)max(c, 0);
+                    if (c < 0) bad |= kErrNegative;
                     if (inter) reinterpret_cast<int2*>(d.N2)[t] = make_int2(c, 0);
                 }
             }
             const uint32_t word = __ballot_sync(kAll, occ);
             if (lane == 0 && (t >> 5) < W) d.bits[0][t >> 5] = word;
         }
-        if (conserved) {
 #pragma unroll
-            for (int dd = 16; dd > 0; dd >>= 1) mine += __shfl_xor_sync(kAll, mine, dd);
-            if (lane == 0 && mine) {
-                if (mine > 2147483647ull) {
-                    atomicOr(&total[1], 1u);
-                } else {
-                    const uint32_t old = atomicAdd(&total[0], (uint32_t)mine);
-                    if ((unsigned long long)old + mine > 2147483647ull) atomicOr(&total[1], 1u);
-                }
+        for (int dd = 16; dd > 0; dd >>= 1) mine += __shfl_xor_sync(kAll, mine, dd);
+        if (lane == 0 && mine) atomicAdd(&mass[0], mine);
+        // The molecule total after a period, kept below 2^32 - 1: then no
+        // int32 count can wrap past 2^32 unseen (see PeriodView::scatter).
+        // Reactions change it; the slow pass adds their net change.
+        auto account = [&](int q) {
+            if (rank == 0 && threadIdx.x == 0) {
+                unsigned long long* dq = &mass[1 + (q & 1)];
+                mass[0] += *dq;
+                *dq = 0ull;
+                if ((long long)mass[0] >= 4294967295ll) atomicOr(err, kErrOverflow);
             }
-        }
-        bool exact = true;
+        };
         for (int q = d.q0; q < d.q1; ++q) {
             csync();   // the previous period's adds and bits are complete
-            if (q == d.q0) exact = !conserved || total[1] != 0u;
+            if (q > d.q0) account(q - 1);
             LightState st{0u, 0, 0, 0, 0, 0, 0, 0ull};
             for (;;) {
-                st = light_pass<SA, kReact, kC>(descs + slot, mps + slot, q, exact, err, st);
+                st = light_pass<SA, kReact, kC>(descs + slot, mps + slot, q, err, st);
                 bad |= st.bad;
                 item_done += st.done;
-                if (st.n_slow > 0) bad |= slow_pass<SA, kReact, kC>(descs + slot, mps + slot, q, exact, err, st.n_slow);
+                if (st.n_slow > 0)
+                    bad |= slow_pass<SA, kReact, kC>(descs + slot, mps + slot, q, err, st.n_slow, &mass[1 + (q & 1)]);
                 if (st.finished) break;
             }
         }
         csync();   // every add of the slice is complete
-        if (inter) {
-            // the slice's counts are in the pairs' half (q1 - q0) & 1; hand
-            // them back in N[0]
+        account(d.q1 - 1);
+        // a count the last period's adds took past 2^31-1 reads negative
+        {
             const int half = (d.q1 - d.q0) & 1;
-            for (int t = rank * kRunBlock + threadIdx.x; t < T; t += kC * kRunBlock) d.N[0][t] = d.N2[2 * t + half];
+            for (int t = rank * kRunBlock + threadIdx.x; t < T; t += kC * kRunBlock) {
+                if (inter) {
+                    // the slice's counts are in the pairs' half (q1 - q0) & 1;
+                    // hand them back in N[0]
+                    const int32_t c = d.N2[2 * t + half];
+                    if (c < 0) bad |= kErrOverflow;
+                    d.N[0][t] = c;
+                } else {
+                    for (int s = 0; s < S; ++s)
+                        if (d.N[half][(int64_t)s * T + t] < 0) bad |= kErrOverflow;
+                }
+            }
         }
         if (bad) atomicOr(err, bad);
         done += item_done;

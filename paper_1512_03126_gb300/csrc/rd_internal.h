@@ -110,10 +110,19 @@ struct PeriodArgs {
     const uint4* thr;       // [S][T] cumulative 32-bit face thresholds for tau_k
     const int32_t* in_prev; // [T][4][Sp] inboxes filled by the previous period
     int32_t* in_cur;        // [T][4][Sp] inboxes this period fills
+    int32_t t_lo = 0;       // the period advances the stored tets [t_lo, t_hi) (a
+    int32_t t_hi = 0;       // rank's range; 0, 0: all tets)
 };
 void launch_period(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a, int block,
                    cudaStream_t st);
-void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int32_t* in_last, cudaStream_t st);
+void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int32_t* in_last, cudaStream_t st,
+                   int32_t t_lo = 0, int32_t t_hi = 0);
+// Copy inbox slots out of / into a packed buffer int32 [n][S] (the transfers
+// across the cut faces of a partitioned mesh).
+void launch_inbox_export(int32_t S, const int32_t* inbox, const int32_t* slots, int32_t n, int32_t* buf,
+                         cudaStream_t st);
+void launch_inbox_import(int32_t S, int32_t* inbox, const int32_t* slots, int32_t n, const int32_t* buf,
+                         cudaStream_t st);
 // The period in two passes (light pass, then the deferred tets): queue holds
 // T entries, qcount two counters (both zero before the first period of a
 // run; parity alternates 0, 1, 0, ... over the run's periods); `block` is the

@@ -286,8 +286,9 @@ template <int S_, bool kReact>
 __global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, DevState s, PeriodArgs a) {
     constexpr int SA = S_ > 0 ? S_ : kMaxS;
     const int S = S_ > 0 ? S_ : mp.S;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = t < m.T;          // every lane stays for the warp draw
+    const int t_hi = a.t_hi > 0 ? a.t_hi : m.T;
+    const int t = a.t_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < t_hi;         // every lane stays for the warp draw
     const int T = m.T;
     const int Sp = inbox_stride(S);
     int32_t N[SA];
@@ -314,7 +315,8 @@ __global__ void __launch_bounds__(kBlock) k_period(DevMesh m, ModelParams mp, De
 template <int S_>
 void launch_period_s(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a, int block,
                      cudaStream_t st) {
-    const int grid = (int)(((int64_t)m.T + block - 1) / block);
+    const int64_t n = (a.t_hi > 0 ? a.t_hi : m.T) - a.t_lo;
+    const int grid = (int)((n + block - 1) / block);
     if (mp.any_reaction) k_period<S_, true><<<grid, block, 0, st>>>(m, mp, s, a);
     else k_period<S_, false><<<grid, block, 0, st>>>(m, mp, s, a);
 }
@@ -348,8 +350,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_period_light(DevMesh m, ModelPara
                                                             int32_t parity) {
     constexpr int SA = S_ > 0 ? S_ : kMaxS;
     const int S = S_ > 0 ? S_ : mp.S;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = t < m.T;          // every lane stays for the warp draw
+    const int t_hi = a.t_hi > 0 ? a.t_hi : m.T;
+    const int t = a.t_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < t_hi;         // every lane stays for the warp draw
     const int T = m.T;
     const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) qcount[parity ^ 1] = 0;
@@ -448,7 +451,8 @@ int sm_count() {
 template <int S_>
 void launch_split_s(const DevMesh& m, const ModelParams& mp, const DevState& s, const PeriodArgs& a,
                     int32_t* queue, int32_t* qcount, int32_t parity, int block, cudaStream_t st) {
-    const int grid = (int)(((int64_t)m.T + block - 1) / block);
+    const int64_t n = (a.t_hi > 0 ? a.t_hi : m.T) - a.t_lo;
+    const int grid = (int)((n + block - 1) / block);
     const int grid_slow = std::min(grid_for(m.T), 2 * sm_count());
     if (mp.any_reaction) {
         k_period_light<S_, true><<<grid, block, 0, st>>>(m, mp, s, a, queue, qcount, parity);
@@ -472,9 +476,10 @@ void launch_period_split(const DevMesh& m, const ModelParams& mp, const DevState
     g_launches += 2;
 }
 
-__global__ void k_gather(DevMesh m, int32_t S, DevState s, const int32_t* __restrict__ in_last) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.T) return;
+__global__ void k_gather(DevMesh m, int32_t S, DevState s, const int32_t* __restrict__ in_last, int32_t t_lo,
+                         int32_t t_hi) {
+    int t = t_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= t_hi) return;
     const int T = m.T;
     const int Sp = inbox_stride(S);
     const int32_t* box = in_last + (int64_t)t * 4 * Sp;
@@ -489,8 +494,40 @@ __global__ void k_gather(DevMesh m, int32_t S, DevState s, const int32_t* __rest
     if (bad) atomicOr(s.err, bad);
 }
 
-void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int32_t* in_last, cudaStream_t st) {
-    k_gather<<<grid_for(m.T), kBlock, 0, st>>>(m, S, s, in_last);
+void launch_gather(const DevMesh& m, int32_t S, const DevState& s, const int32_t* in_last, cudaStream_t st,
+                   int32_t t_lo, int32_t t_hi) {
+    if (t_hi <= 0) t_hi = m.T;
+    k_gather<<<grid_for(t_hi - t_lo), kBlock, 0, st>>>(m, S, s, in_last, t_lo, t_hi);
+    ++g_launches;
+}
+
+__global__ void k_inbox_export(int32_t S, const int32_t* __restrict__ inbox, const int32_t* __restrict__ slots,
+                               int32_t n, int32_t* __restrict__ buf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * S) return;
+    const int64_t k = i / S, sp = i - k * S;
+    buf[i] = inbox[(int64_t)slots[k] * inbox_stride(S) + sp];
+}
+
+__global__ void k_inbox_import(int32_t S, int32_t* __restrict__ inbox, const int32_t* __restrict__ slots,
+                               int32_t n, const int32_t* __restrict__ buf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * S) return;
+    const int64_t k = i / S, sp = i - k * S;
+    inbox[(int64_t)slots[k] * inbox_stride(S) + sp] = buf[i];
+}
+
+void launch_inbox_export(int32_t S, const int32_t* inbox, const int32_t* slots, int32_t n, int32_t* buf,
+                         cudaStream_t st) {
+    if (n <= 0) return;
+    k_inbox_export<<<grid_for((int64_t)n * S), kBlock, 0, st>>>(S, inbox, slots, n, buf);
+    ++g_launches;
+}
+
+void launch_inbox_import(int32_t S, int32_t* inbox, const int32_t* slots, int32_t n, const int32_t* buf,
+                         cudaStream_t st) {
+    if (n <= 0) return;
+    k_inbox_import<<<grid_for((int64_t)n * S), kBlock, 0, st>>>(S, inbox, slots, n, buf);
     ++g_launches;
 }
 

@@ -56,6 +56,11 @@ def _declare(L):
         "rdsplit_set_allocator": ([vp, vp, vp], C.c_int),
         "rdsplit_set_timing": ([vp, i32], C.c_int),
         "rdsplit_set_period_kernel": ([vp, i32, i32], C.c_int),
+        "rdsplit_partition_set": ([vp, i32, i32], C.c_int),
+        "rdsplit_partition_step": ([vp, dbl, u64, C.POINTER(i32)], C.c_int),
+        "rdsplit_inbox_export": ([vp, vp, i32, vp], C.c_int),
+        "rdsplit_inbox_import": ([vp, vp, i32, vp], C.c_int),
+        "rdsplit_partition_end": ([vp], C.c_int),
         "rdsplit_get_period_kernel": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "rdsplit_static_scratch_bytes": ([i32, i32, i32], C.c_size_t),
         "rdsplit_engine_create": ([i32, i64, C.POINTER(vp)], C.c_int),
@@ -232,6 +237,31 @@ def rdsplit_set_stream(h, stream):
 
 def rdsplit_mesh_destroy(h):
     _check(lib().rdsplit_mesh_destroy(h))
+
+
+def rdsplit_partition_set(h, t0: int, t1: int):
+    _check(lib().rdsplit_partition_set(h, int(t0), int(t1)))
+
+
+def rdsplit_partition_step(h, t_end: float, seed: int) -> bool:
+    """One period of the own tets; True while t < t_end."""
+    more = C.c_int32()
+    _check(lib().rdsplit_partition_step(h, float(t_end), int(seed), C.byref(more)))
+    return bool(more.value)
+
+
+def rdsplit_inbox_export(h, d_slots, d_buf):
+    """d_slots: int32 device tensor [n]; d_buf: int32 device tensor [n][S]."""
+    _check(lib().rdsplit_inbox_export(h, _ptr(d_slots), int(d_slots.numel()), _ptr(d_buf)))
+    return d_buf
+
+
+def rdsplit_inbox_import(h, d_slots, d_buf):
+    _check(lib().rdsplit_inbox_import(h, _ptr(d_slots), int(d_slots.numel()), _ptr(d_buf)))
+
+
+def rdsplit_partition_end(h):
+    _check(lib().rdsplit_partition_end(h))
 
 
 def rdsplit_set_period_kernel(h, mode: int = 0, block: int = 0):

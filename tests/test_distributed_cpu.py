@@ -5,8 +5,9 @@
    of the per-rank times.
 2. The paper's parallel scheme (Sec. III.D, domain decomposition): each rank
    advances its own contiguous range of tets for a period (the oracle's
-   per-range Steps 2-3), the out-slots are exchanged once per period, and
-   each rank applies what its tets receive.  Because every draw is keyed by
+   per-range Steps 2-3), the transfers across cut faces (and only those) go
+   to the rank that owns the receiving tet once per period, in the order of
+   partition.cut_slots, and each rank applies what its tets receive.  Because every draw is keyed by
    the canonical tet id, the result must equal the single-process run bit
    for bit, for any number of ranks.
 """
@@ -78,13 +79,18 @@ def _dd_worker(rank, world, port, outpath):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
     from oracle import oracle as O
+    from paper_1512_03126_gb300 import partition as P
     dist = _init(rank, world, port)
     w = _dd_workload()
     T, S = w.mesh.n_tets, w.model.n_species
-    bounds = [T * r // world for r in range(world + 1)]
-    lo, hi = bounds[rank], bounds[rank + 1]
-    width = max(bounds[r + 1] - bounds[r] for r in range(world))
-    rev = _reverse(w.mesh.adj)
+    adj = w.mesh.adj
+    parts = P.ranges(T, world)
+    lo, hi = parts[rank]
+    rev = _reverse(adj)
+    # face f of the writer t = adj[u][r] that points at u
+    face_to = lambda t, u: int(np.nonzero(adj[t] == u)[0][0])
+    sends = {p: P.cut_slots(adj, (lo, hi), parts[p]) for p in range(world) if p != rank}
+    recvs = {p: P.cut_slots(adj, parts[p], (lo, hi)) for p in range(world) if p != rank}
     N = np.zeros((T, S), np.int32)
     N[lo:hi] = w.counts[lo:hi]            # a rank holds only its own tets
     tau = O.tau(w.mesh, w.model)
@@ -94,32 +100,69 @@ def _dd_worker(rank, world, port, outpath):
         if t_now + tau > w.t_end:
             tau_k, last = w.t_end - t_now, True
         out, rem = O.period_tets(w.mesh, w.model, N, period, tau_k, w.seed, lo, hi)
-        # the one exchange of the period: every rank's out-slots
-        pad = np.zeros((width, S, 4), np.int32)
-        pad[:hi - lo] = out
-        parts = [torch.zeros((width, S, 4), dtype=torch.int32) for _ in range(world)]
-        dist.all_gather(parts, torch.from_numpy(pad))
-        full = np.concatenate([parts[r].numpy()[:bounds[r + 1] - bounds[r]] for r in range(world)])
+        # the one exchange of the period: the transfers across cut faces
+        # only, to the rank that owns the receiving tet
+        reqs, got = [], {}
+        for p, sl in sends.items():
+            buf = np.zeros((len(sl), S), np.int32)
+            for k, slot in enumerate(sl):
+                u, r = divmod(int(slot), 4)
+                t = int(adj[u, r])
+                buf[k] = out[t - lo, :, face_to(t, u)]
+            reqs.append(dist.isend(torch.from_numpy(buf), dst=p))
+        for p, sl in recvs.items():
+            got[p] = torch.zeros((len(sl), S), dtype=torch.int32)
+            reqs.append(dist.irecv(got[p], src=p))
+        for q in reqs:
+            q.wait()
+        incoming = np.zeros((T, S), np.int64)
+        for p, sl in recvs.items():
+            for k, slot in enumerate(sl):
+                u = int(slot) // 4
+                incoming[u] += got[p].numpy()[k]
         # synchronous apply for this rank's tets
         N[:] = 0
         for t in range(lo, hi):
-            v = rem[t - lo].astype(np.int64)
+            v = rem[t - lo].astype(np.int64) + incoming[t]
             for f in range(4):
-                u = w.mesh.adj[t, f]
-                if u >= 0:
-                    v = v + full[u, :, rev[t, f]]
+                u = adj[t, f]
+                if lo <= u < hi:
+                    v = v + out[u - lo, :, rev[t, f]]
             N[t] = v
         t_now = w.t_end if last else t_now + tau
         period += 1
-    mine = torch.from_numpy(np.ascontiguousarray(N[lo:hi]))
+    width = max(b - a for a, b in parts)
     pad = torch.zeros((width, S), dtype=torch.int32)
-    pad[:hi - lo] = mine
-    parts = [torch.zeros((width, S), dtype=torch.int32) for _ in range(world)]
-    dist.all_gather(parts, pad)
+    pad[:hi - lo] = torch.from_numpy(np.ascontiguousarray(N[lo:hi]))
+    allparts = [torch.zeros((width, S), dtype=torch.int32) for _ in range(world)]
+    dist.all_gather(allparts, pad)
     if rank == 0:
-        final = np.concatenate([parts[r].numpy()[:bounds[r + 1] - bounds[r]] for r in range(world)])
+        final = np.concatenate([allparts[r].numpy()[:parts[r][1] - parts[r][0]] for r in range(world)])
         np.save(outpath, final)
     dist.destroy_process_group()
+
+
+def test_cut_slots_pair_up():
+    """Each cut face appears once, in the sender's export list and in the
+    receiver's import list (the same list), and only cut faces do."""
+    from paper_1512_03126_gb300 import partition as P
+    w = _dd_workload()
+    adj = w.mesh.adj
+    parts = P.ranges(w.mesh.n_tets, 3)
+    seen = set()
+    for a in range(3):
+        for b in range(3):
+            if a == b:
+                continue
+            sl = P.cut_slots(adj, parts[a], parts[b])
+            assert np.all(np.diff(sl) > 0)
+            for slot in sl:
+                u, r = divmod(int(slot), 4)
+                assert parts[b][0] <= u < parts[b][1] and parts[a][0] <= adj[u, r] < parts[a][1]
+                seen.add(int(slot))
+    cut = {4 * u + r for u in range(w.mesh.n_tets) for r in range(4)
+           if adj[u, r] >= 0 and [lo <= u < hi for lo, hi in parts] != [lo <= adj[u, r] < hi for lo, hi in parts]}
+    assert seen == cut
 
 
 @pytest.mark.parametrize("world", [2, 3])

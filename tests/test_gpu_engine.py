@@ -235,3 +235,57 @@ def test_deferred_queue_overflow_and_resume(rd, oracle):
             finally:
                 rd.rdsplit_engine_destroy(e)
             assert np.array_equal(s.counts(), ref), cluster
+
+
+def _line_of_three():
+    """Tets A - B - C; A and C have half B's volume, so zeta = 1 in them (every
+    molecule leaves each period) and 1/2 in B."""
+    from paper_1512_03126_gb300.inputs import Mesh
+    adj = np.array([[1, -1, -1, -1], [0, 2, -1, -1], [1, -1, -1, -1]], np.int32)
+    area = np.zeros((3, 4))
+    dist = np.zeros((3, 4))
+    area[0, 0] = area[1, 0] = area[1, 1] = area[2, 0] = 1e-13
+    dist[0, 0] = dist[1, 0] = dist[1, 1] = dist[2, 0] = 2e-7
+    return Mesh(adj=adj, vol=np.array([1e-19, 4e-19, 1e-19]), area=area, dist=dist,
+                centroid=np.array([[0, 0, 0], [2e-7, 0, 0], [4e-7, 0, 0]], np.float64), shape=(), size=(1, 1, 1))
+
+
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_count_overflow_is_reported_like_the_oracle(rd, oracle, cluster):
+    """A count pushed past 2^31-1 by the transfers: A and C each hold 1.2e9
+    molecules and send all of them to B in the first period.  The oracle,
+    the period kernel and the batched engine (whose adds are fire-and-forget:
+    the wrapped count is caught when read back) all report the overflow;
+    with 1.0e9 each none does, and the three agree."""
+    m = _line_of_three()
+    model = I.diffusion_model(1e-12)
+    for each, overflows in ((1_200_000_000, True), (1_000_000_000, False)):
+        c0 = np.array([[each], [0], [each]], np.int32)
+        if overflows:
+            with pytest.raises(oracle.OracleError):
+                oracle.run(m, model, c0, np.inf, 3, max_periods=2)
+        else:
+            ref, _, _ = oracle.run(m, model, c0, np.inf, 3, max_periods=2)
+        with rd.Simulation(m, model, c0) as s:
+            if overflows:
+                with pytest.raises(rd.RdsplitError) as e:
+                    s.run_periods(2, 3)
+                assert e.value.code == rd.RDSPLIT_EOVERFLOW
+            else:
+                s.run_periods(2, 3)
+                assert np.array_equal(s.counts(), ref)
+        with rd.Simulation(m, model, c0) as s:
+            tau = s.tau
+            e = rd.rdsplit_engine_create(1, 3)
+            try:
+                rd.rdsplit_engine_set_concurrency(e, 1, cluster)
+                rd.rdsplit_engine_add(e, s.h, 2 * tau, 3)
+                if overflows:
+                    with pytest.raises(rd.RdsplitError) as err:
+                        rd.rdsplit_engine_step(e, 1 << 30)
+                    assert err.value.code == rd.RDSPLIT_EOVERFLOW
+                else:
+                    rd.rdsplit_engine_step(e, 1 << 30)
+                    assert np.array_equal(s.counts(), ref)
+            finally:
+                rd.rdsplit_engine_destroy(e)
