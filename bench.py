@@ -461,7 +461,8 @@ def run_ensemble(args, rank, world, local_rank):
             done += w.mesh.n_tets * p
             k += 1
         dt = time.perf_counter() - t0
-        cpu = {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+               "host_cores": host_cores(),
                "sample": f"first {args.cpu_periods} periods of instances 0..{k - 1} of the ensemble, "
                          f"one host core, {dt:.1f} s"}
 
@@ -806,7 +807,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     periods_per_step = max(1, int(args.ref_periods))
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     name = "batched ensemble (instance c on host core c)" if args.workload == "ensemble" else args.workload
     try:
         done, secs = _reference_all_cores(args, cores)
@@ -836,7 +837,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32 counts, f64 rates",
             "data": "synthetic", "config": {"workload": name, "periods_per_step": periods_per_step,
-                                            "host_cores": cores, "per_core_value": value / cores},
+                                            "host_cores": cores, "per_core_value": value / cores,
+                                            "cpu_model": cpu_model()},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
