@@ -201,8 +201,9 @@ struct PeriodView {
 // appends the set bits of each column to its list in shared memory
 // (a prefix sum of the lanes' popcounts gives each lane its place); whenever
 // the list holds 32 tets, one round takes them, one per lane.  A round runs
-// every tet that needs no non-inlined sampler (step_is_light) with the
-// call-free step, and queues the others for the slow pass.  Kept out of
+// every tet that needs neither a non-inlined sampler (step_is_light) nor a
+// whole-warp draw (10 or more molecules of a species) with the call-free
+// step, and queues the others for the slow pass.  Kept out of
 // line, and free of calls, so that the compiler allocates its registers
 // without the double-precision samplers' demands.  Returns early, with a
 // resume point, when the next round could overflow the queue.
@@ -248,6 +249,13 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
                 }
             }
             light = step_is_light<SA, kReact>(d.m, mp, v.period, v.tau_kf, d.seed, t, v.S, N);
+            // tets whose draws need the whole warp (warp_split) go to the slow
+            // pass too, which keeps the light pass free of that loop
+#pragma unroll
+            for (int s = 0; s < SA; ++s) {
+                if (s >= v.S) break;
+                if (N[s] >= kWarpSplitMin) light = false;
+            }
         }
         const unsigned slow_mask = __ballot_sync(kAll, live && !light);
         if (live && !light) slowq[st.n_slow + __popc(slow_mask & lane_lt)] = t;
@@ -261,8 +269,6 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
             st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
                                                  &heavy, err, v.tstride, v.use_packed, pre);
         }
-        warp_split<SA>(heavy, d.seed, v.period, t, live ? key_of(d.m, t) : 0, v.thr, v.T, N, o, v.tstride,
-                       v.use_packed, pre);
         if (light) st.bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
     };
 
