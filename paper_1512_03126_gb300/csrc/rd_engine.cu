@@ -582,6 +582,7 @@ struct EngineLaunch {
     int clusters;
     int used = 0;         // clusters launched
     int max_active = 0;   // clusters resident at once (occupancy query)
+    bool query_only = false;   // fill max_active, launch nothing
 };
 
 template <int SA, bool R, int C>
@@ -613,6 +614,7 @@ cudaError_t launch_cluster(EngineLaunch& L) {
     cudaGetLastError();
     if (fit <= 0) fit = std::max(1, L.sms / C);
     L.max_active = fit;
+    if (L.query_only) return cudaSuccess;
     int n = L.clusters > 0 ? std::min(L.clusters, fit) : fit;
     n = std::max(1, std::min(n, L.n_items));
     L.used = n;
@@ -657,6 +659,10 @@ struct rdsplit_engine {
     int32_t last_in_flight = 0;               // clusters of the last launch
     int32_t last_max_active = 0;              // clusters that fit at once in the last launch
     int64_t slice_work = 0;                   // tet-periods per simulation and step call (0: no limit)
+    int32_t last_groups = 0;                  // kernel groups of the last launch
+    cudaStream_t aux[10] = {};                // one stream per kernel group
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[10] = {};
     int32_t cluster = 2;                      // CTAs per simulation (1, 2 or 4)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
@@ -668,6 +674,11 @@ struct rdsplit_engine {
     ~rdsplit_engine() {
         for (cudaEvent_t x : ev)
             if (x) cudaEventDestroy(x);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (cudaEvent_t x : ev_join)
+            if (x) cudaEventDestroy(x);
+        for (cudaStream_t x : aux)
+            if (x) cudaStreamDestroy(x);
         void* ps[] = {d_desc, d_mp, d_order, d_head, err, processed, d_times};
         for (void* p : ps) rdapi::dev_free(p);
     }
@@ -737,7 +748,7 @@ int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_en
     e->d_desc = (SlotDesc*)rdapi::dev_alloc(sizeof(SlotDesc) * max_slots);
     e->d_mp = (ModelParams*)rdapi::dev_alloc(sizeof(ModelParams) * max_slots);
     e->d_order = (int32_t*)rdapi::dev_alloc(sizeof(int32_t) * max_slots);
-    e->d_head = (int32_t*)rdapi::dev_alloc(sizeof(int32_t));
+    e->d_head = (int32_t*)rdapi::dev_alloc(sizeof(int32_t) * 10);
     e->err = (uint32_t*)rdapi::dev_alloc(sizeof(uint32_t));
     e->processed = (unsigned long long*)rdapi::dev_alloc(sizeof(unsigned long long));
     e->d_times = (unsigned long long*)rdapi::dev_alloc(sizeof(unsigned long long) * 4 * max_slots);
@@ -862,8 +873,6 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
     if (n_steps <= 0) return RDSPLIT_OK;
     std::vector<int32_t> items;
     std::vector<double> work;
-    int maxS = 1;
-    bool react = false;
     int64_t max_adv = 0;
     for (int s = 0; s < e->max_slots; ++s) {
         rdsplit_mesh* h = e->slot_mesh[s];
@@ -878,47 +887,128 @@ int rdsplit_engine_step(rdsplit_engine_t e, int64_t n_steps) {
         d.q1 = (int32_t)std::min<int64_t>((int64_t)d.P, (int64_t)d.q0 + n);
         if (d.q1 <= d.q0) continue;
         items.push_back(s);
-        work.push_back((double)(d.q1 - d.q0) * (double)h->T);
-        maxS = std::max(maxS, d.S);
-        react = react || h->R > 0;
+        work.push_back((double)(d.q1 - d.q0) * (double)h->T * (double)h->S);
         max_adv = std::max<int64_t>(max_adv, d.q1 - d.q0);
     }
     if (items.empty()) return engine_err(e, where);
-    // largest first
+    // Simulations are launched in groups of one kernel instantiation each:
+    // species class (1, 2, up to 4, up to 8, more) and with or without
+    // reactions, so that a one-species simulation does not run the code
+    // sized for eight.  Groups run concurrently on their own streams, the
+    // resident clusters shared among them by work; largest first in each.
+    auto cls_of = [&](int s) {
+        const rdsplit_mesh* h = e->slot_mesh[s];
+        const int S = h->S;
+        const int c = S <= 1 ? 0 : (S <= 2 ? 1 : (S <= 4 ? 2 : (S <= 8 ? 3 : 4)));
+        return 2 * c + (h->R > 0 ? 1 : 0);
+    };
+    constexpr int kGroups = 10;
     std::vector<size_t> idx(items.size());
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+        const int ga = cls_of(items[a]), gb = cls_of(items[b]);
+        return ga != gb ? ga < gb : work[a] > work[b];
+    });
     std::vector<int32_t> order(items.size());
-    for (size_t k = 0; k < idx.size(); ++k) order[k] = items[idx[k]];
+    int g_begin[kGroups + 1] = {0};
+    double g_work[kGroups] = {0.0};
+    int g_count[kGroups] = {0};
+    for (size_t k = 0; k < idx.size(); ++k) {
+        order[k] = items[idx[k]];
+        const int g = cls_of(order[k]);
+        g_count[g] += 1;
+        g_work[g] += work[idx[k]];
+    }
+    for (int g = 0; g < kGroups; ++g) g_begin[g + 1] = g_begin[g] + g_count[g];
+    int n_groups = 0;
+    for (int g = 0; g < kGroups; ++g) n_groups += g_count[g] > 0 ? 1 : 0;
     cudaStream_t st = e->stream;
     cudaError_t ce = cudaMemcpyAsync(e->d_desc, e->h_desc.data(), sizeof(SlotDesc) * e->max_slots,
                                      cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(e->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->d_head, 0, sizeof(int32_t), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->d_head, 0, sizeof(int32_t) * kGroups, st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return rdapi::fail(RDSPLIT_ECUDA, "%s: upload failed: %s", where, cudaGetErrorString(ce));
     }
-    const int n_items = (int)order.size();
     const int csize = e->cluster;
-    // default: as many clusters as can be resident at once (one CTA per SM
-    // where the GPCs allow it).  More simulations in flight than that would
-    // spill their scattered working sets out of L2.
     if (e->timing && !e->ev[0]) {
         cudaEventCreate(&e->ev[0]);
         cudaEventCreate(&e->ev[1]);
     }
     if (e->timing) cudaEventRecord(e->ev[0], st);
-    EngineLaunch L{e->d_desc, e->d_mp, e->d_order, n_items, e->d_head, e->err, e->processed,
-                   e->timing ? e->d_times : nullptr, st, e->sms, e->concurrency};
-    if (maxS <= 1) ce = launch_run_sa<1>(react, csize, L);
-    else if (maxS <= 2) ce = launch_run_sa<2>(react, csize, L);
-    else if (maxS <= 4) ce = launch_run_sa<4>(react, csize, L);
-    else if (maxS <= 8) ce = launch_run_sa<8>(react, csize, L);
-    else ce = launch_run_sa<kMaxS>(react, csize, L);
+    auto launch_group = [&](int g, EngineLaunch& L) -> cudaError_t {
+        const bool react = (g & 1) != 0;
+        switch (g >> 1) {
+            case 0: return launch_run_sa<1>(react, csize, L);
+            case 1: return launch_run_sa<2>(react, csize, L);
+            case 2: return launch_run_sa<4>(react, csize, L);
+            case 3: return launch_run_sa<8>(react, csize, L);
+            default: return launch_run_sa<kMaxS>(react, csize, L);
+        }
+    };
+    int used = 0, fit = 0;
+    if (n_groups == 1) {
+        int g = 0;
+        while (g_count[g] == 0) ++g;
+        // default: as many clusters as can be resident at once (one CTA per
+        // SM where the GPCs allow it)
+        EngineLaunch L{e->d_desc, e->d_mp, e->d_order, g_count[g], e->d_head, e->err, e->processed,
+                       e->timing ? e->d_times : nullptr, st, e->sms, e->concurrency};
+        ce = launch_group(g, L);
+        used = L.used;
+        fit = L.max_active;
+    } else {
+        // the clusters that fit, shared by work (at least one per group)
+        EngineLaunch Q{e->d_desc, e->d_mp, e->d_order, 1, e->d_head, e->err, e->processed, nullptr, st, e->sms, 0};
+        Q.query_only = true;
+        ce = launch_group(7, Q);
+        fit = Q.max_active;
+        const int budget = e->concurrency > 0 ? std::min(e->concurrency, fit) : fit;
+        double total = 0.0;
+        for (int g = 0; g < kGroups; ++g) total += g_work[g];
+        int share[kGroups] = {0};
+        int given = 0;
+        for (int g = 0; g < kGroups; ++g) {
+            if (!g_count[g]) continue;
+            share[g] = std::max(1, (int)((double)budget * g_work[g] / std::max(total, 1.0)));
+            share[g] = std::min(share[g], g_count[g]);
+            given += share[g];
+        }
+        while (given > std::max(budget, n_groups)) {   // trim the largest shares
+            int gm = -1;
+            for (int g = 0; g < kGroups; ++g)
+                if (share[g] > 1 && (gm < 0 || share[g] > share[gm])) gm = g;
+            if (gm < 0) break;
+            share[gm] -= 1;
+            given -= 1;
+        }
+        if (!e->ev_fork) {
+            cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming);
+            for (int g = 0; g < kGroups; ++g) {
+                cudaStreamCreateWithFlags(&e->aux[g], cudaStreamNonBlocking);
+                cudaEventCreateWithFlags(&e->ev_join[g], cudaEventDisableTiming);
+            }
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(e->ev_fork, st);
+        for (int g = 0; g < kGroups && ce == cudaSuccess; ++g) {
+            if (!g_count[g]) continue;
+            ce = cudaStreamWaitEvent(e->aux[g], e->ev_fork, 0);
+            EngineLaunch L{e->d_desc, e->d_mp, e->d_order + g_begin[g], g_count[g], e->d_head + g, e->err,
+                           e->processed, e->timing ? e->d_times : nullptr, e->aux[g], e->sms, share[g]};
+            if (ce == cudaSuccess) ce = launch_group(g, L);
+            used += L.used;
+            if (ce == cudaSuccess) ce = cudaEventRecord(e->ev_join[g], e->aux[g]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, e->ev_join[g], 0);
+        }
+    }
+    EngineLaunch L{};
+    L.used = used;
+    L.max_active = fit;
     e->last_in_flight = L.used;
     e->last_max_active = L.max_active;
+    e->last_groups = n_groups;
     if (e->timing) cudaEventRecord(e->ev[1], st);
     note_launch();
     e->launches += 1;
