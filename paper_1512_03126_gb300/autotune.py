@@ -89,7 +89,7 @@ def _timed(fn, stream) -> float:
     return e0.elapsed_time(e1)
 
 
-DENSE_CANDIDATES = [(1, 64), (1, 128), (1, 256), (2, 128), (2, 256)]
+DENSE_CANDIDATES = [(1, 32), (1, 64), (1, 128), (1, 256), (2, 64), (2, 256)]
 
 
 def tune_period(rd, w, stream, periods: int = 48, candidates=None, use_cache: bool = True) -> dict:

@@ -35,6 +35,11 @@ struct ModelParams {
     int8_t rs1[kMaxR], rs2[kMaxR];
     float kf[kMaxR];
     uint32_t kpos;
+    // Per species: the reactions that consume it, and those that consume two
+    // of it (2A): a reaction is possible in a tet unless a species it needs
+    // is absent (or, for 2A, present only once).
+    uint32_t needs[kMaxS];
+    uint32_t needs2[kMaxS];
     // Transfer rule of the diffusion draw (Sec. II.C): kRuleMean (N-bar,
     // Eq. 3, the method), kRuleEnd (N at tau_k, first-order splitting) or
     // kRuleMid (N at tau_k / 2).

@@ -227,6 +227,7 @@ void launch_counts_out(int32_t T, int32_t S, const int32_t* sm, int32_t* ts, con
 // ---------------------------------------------------------------- period ---
 void finish_model_params(ModelParams& mp) {
     mp.kpos = 0;
+    for (int s = 0; s < kMaxS; ++s) mp.needs[s] = mp.needs2[s] = 0u;
     for (int r = 0; r < mp.R; ++r) {
         mp.rs1[r] = mp.rs2[r] = -1;
         for (int s = 0; s < mp.S; ++s) {
@@ -238,6 +239,10 @@ void finish_model_params(ModelParams& mp) {
         }
         mp.kf[r] = (float)mp.k[r];
         if (mp.k[r] > 0.0) mp.kpos |= 1u << r;
+        for (int s = 0; s < mp.S; ++s) {
+            if (mp.lhs[r][s] >= 1) mp.needs[s] |= 1u << r;
+            if (mp.lhs[r][s] >= 2) mp.needs2[s] |= 1u << r;
+        }
     }
 }
 

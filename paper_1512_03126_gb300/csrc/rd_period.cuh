@@ -285,7 +285,9 @@ __device__ __forceinline__ float combos_f(const ModelParams& mp, int r, const in
     return (float)na * (float)pick<SA>(N, b);
 }
 
-// True only if the exact SSA of this tet would draw no event in this period:
+// True only if the exact SSA of this tet would draw no event in this period
+// (`on`: the reactions that can fire, in ascending order as the SSA sums
+// them):
 // with u1 the stream's first uniform, the first event time is
 // -log(u1)/a0 >= (1-u1)/a0, so (1-u1) >= a0 tau_k (1 + margin) rules an event
 // out.  a0 and the products are evaluated in single precision; their relative
@@ -298,9 +300,8 @@ template <int SA>
 __device__ __forceinline__ bool surely_no_event(const ModelParams& mp, const int32_t* N, uint32_t on, float2 av,
                                                 uint32_t period, float tau_kf, uint64_t seed, int key) {
     float a0 = 0.0f;
-    const int R = mp.R;
-    for (int r = 0; r < R; ++r) {
-        if (!((on >> r) & 1u)) continue;
+    for (uint32_t bits = on; bits; bits &= bits - 1u) {
+        const int r = __ffs(bits) - 1;
         float h = combos_f<SA>(mp, r, N);
         if (h == 0.0f) continue;
         int o = mp.order[r];
@@ -334,18 +335,19 @@ __device__ __forceinline__ int4 split_molecules(uint64_t seed, uint32_t period, 
 }
 
 
-// Whether some reaction with k > 0 that is on in the tet has its reactants.
+// The reactions (k > 0, on in the tet, given as `on`) whose reactants are
+// present: a species with no molecule rules out every reaction that
+// consumes it, one molecule rules out those that consume two.
 template <int SA>
-__device__ __forceinline__ bool reaction_possible(const ModelParams& mp, const int32_t* N, uint32_t on) {
-    bool possible = false;
-    for (int r = 0; r < mp.R && !possible; ++r) {
-        if (!((on >> r) & 1u)) continue;
-        int ra = mp.rs1[r], rb = mp.rs2[r];
-        int32_t na = ra < 0 ? 1 : pick<SA>(N, ra);
-        int32_t nb = rb < 0 ? 1 : pick<SA>(N, rb);
-        possible = ra < 0 || (rb < 0 ? na > 0 : (ra == rb ? na > 1 : (na > 0 && nb > 0)));
+__device__ __forceinline__ uint32_t possible_reactions(const ModelParams& mp, const int32_t* N, uint32_t on) {
+    uint32_t m = on;
+#pragma unroll
+    for (int s = 0; s < SA; ++s) {
+        if (s >= mp.S) break;
+        if (N[s] <= 0) m &= ~mp.needs[s];
+        else if (N[s] == 1) m &= ~mp.needs2[s];
     }
-    return possible;
+    return m;
 }
 
 // True when step_tet would run neither non-inlined sampler for this tet:
@@ -363,8 +365,9 @@ __device__ __forceinline__ bool step_is_light(const DevMesh& m, const ModelParam
     }
     if (!kReact) return true;
     const uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
-    if (!reaction_possible<SA>(mp, N, on)) return true;
-    return surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, key_of(m, t));
+    const uint32_t poss = possible_reactions<SA>(mp, N, on);
+    if (!poss) return true;
+    return surely_no_event<SA>(mp, N, poss, m.avv[t], period, tau_kf, seed, key_of(m, t));
 }
 
 // Steps 2 and 3 of one period for one tet, given its counts N after the
@@ -391,8 +394,8 @@ __device__ __forceinline__ uint32_t step_tet(const DevMesh& m, const ModelParams
     int64_t nmid[SA];
     if (kReact && kCalls) {
         uint32_t on = (mp.has_mask ? m.mask[t] : 0xffffffffu) & mp.kpos;
-        const bool possible = reaction_possible<SA>(mp, N, on);
-        if (possible && !surely_no_event<SA>(mp, N, on, m.avv[t], period, tau_kf, seed, key)) {
+        const uint32_t poss = possible_reactions<SA>(mp, N, on);
+        if (poss && !surely_no_event<SA>(mp, N, poss, m.avv[t], period, tau_kf, seed, key)) {
             int64_t N64[SA];
             double tl[SA];
 #pragma unroll
