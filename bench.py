@@ -423,6 +423,34 @@ def run_ensemble(args, rank, world, local_rank):
                  "launches": sum(periods) + 2 * n_inst,
                  "form": "one rdsplit_run launch sequence per simulation (dense period kernel)"}
 
+    # the plain engine form: the same engine, one simulation per launch
+    # (4-CTA clusters, the fastest single-simulation shape), on every 8th
+    # instance; separates the gain of batching from that of skipping empty tets
+    plain_engine = None
+    if rank == 0 and not args.no_plain:
+        sample = list(range(0, n_inst, args.plain_engine_stride))
+        e1 = rd.rdsplit_engine_create(1, max(w.mesh.n_tets for w in ws))
+        rd.rdsplit_engine_set_stream(e1, stream)
+        rd.rdsplit_engine_set_concurrency(e1, 1, 4)
+        reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e9 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in sample:
+            rd.rdsplit_engine_add(e1, sims[i].h, ws[i].t_end, seeds[i])
+            rd.rdsplit_engine_step(e1, 1 << 40)
+            rd.rdsplit_engine_poll(e1, 4)
+        e9.record(stream)
+        e9.synchronize()
+        pe_ms = e0.elapsed_time(e9)
+        rd.rdsplit_engine_destroy(e1)
+        pe_units = sum(ws[i].mesh.n_tets * periods[i] for i in sample)
+        plain_engine = {"value": pe_units / (pe_ms / 1e3), "unit": UNIT, "ms": pe_ms, "instances": len(sample),
+                        "form": f"one engine launch per simulation (4-CTA cluster), every "
+                                f"{args.plain_engine_stride}th instance"}
+
     # end to end: host counts in, host counts out, through the public calls
     e2e = None
     if not args.no_e2e:
@@ -494,6 +522,8 @@ def run_ensemble(args, rank, world, local_rank):
         "processed_entries_per_s": entries * args.steps * world / (total_ms / 1e3),
         "roofline": roofline, "tail": tail, "autotune": tuned, "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "plain_engine": plain_engine,
+        "batched_vs_plain_engine": (value / plain_engine["value"]) if plain_engine else None,
         "serving": serving, "configs": configs, "reorder": reorder,
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
     }
@@ -853,6 +883,8 @@ def main():
     ap.add_argument("--instances", type=int, default=0, help="ensemble: use the first N instances (0 = all 512)")
     ap.add_argument("--ensemble-t-end", type=float, default=0.1, help="ensemble: simulated time per instance (s)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-engine-stride", type=int, default=8,
+                    help="ensemble: time the one-simulation-per-launch engine on every Nth instance")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--requests", type=int, default=400, help="serving: number of requests")
     ap.add_argument("--slice", type=int, default=256, help="serving: periods per engine launch")

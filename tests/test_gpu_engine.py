@@ -289,3 +289,25 @@ def test_count_overflow_is_reported_like_the_oracle(rd, oracle, cluster):
                     assert np.array_equal(s.counts(), ref)
             finally:
                 rd.rdsplit_engine_destroy(e)
+
+
+def test_adding_with_t_end_in_the_past_keeps_the_state(rd):
+    """A simulation added with t_end at or before its current time runs no
+    period and keeps its time, period index and counts, as rdsplit_run does
+    for such a t_end."""
+    w = I.diffusion_cube(4, 1e-6, 0.2, 11, 300, 0.004, 3)
+    with rd.Simulation(w.mesh, w.model, w.counts) as a, rd.Simulation(w.mesh, w.model, w.counts) as b:
+        a.run(w.t_end, w.seed)
+        b.run(w.t_end, w.seed)
+        ta, pa = a.time
+        ca = a.counts()
+        a.run(0.5 * w.t_end, w.seed)                 # dense path: a no-op
+        e = rd.rdsplit_engine_create(1, w.mesh.n_tets)
+        try:
+            rd.rdsplit_engine_add(e, b.h, 0.5 * w.t_end, w.seed)
+            rd.rdsplit_engine_step(e, 10)
+            assert rd.rdsplit_engine_active(e)[0] == 0
+        finally:
+            rd.rdsplit_engine_destroy(e)
+        assert a.time == (ta, pa) == b.time
+        assert np.array_equal(a.counts(), ca) and np.array_equal(b.counts(), ca)
