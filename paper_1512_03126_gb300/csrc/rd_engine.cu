@@ -266,8 +266,29 @@ __device__ __noinline__ LightState light_pass(const SlotDesc* __restrict__ dp, c
                 if (s >= v.S) break;
                 v.Ncur[((int64_t)s * v.T + t) * v.cstride] = 0;
             }
-            st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N, o,
-                                                 &heavy, err, v.tstride, v.use_packed, pre);
+            if (SA == 1 && !kReact && v.use_packed && N[0] <= 4) {
+                // one species, at most four molecules: the first Philox
+                // block of the tet's diffusion stream holds all their draws
+                // (the words split_molecules would take, in its order)
+                const uint32_t key = (uint32_t)key_of(d.m, t);
+                const uint4 w = rdd::philox_block(0u, key, v.period, rdd::kPurposeDiffusion << 16,
+                                                  (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+                const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+                int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= N[0]) break;
+                    if (rdd::below(u[i], pre.x)) ++c0;
+                    else if (rdd::below(u[i], pre.y)) ++c1;
+                    else if (rdd::below(u[i], pre.z)) ++c2;
+                    else if (rdd::below(u[i], pre.w)) ++c3;
+                }
+                o[0] = make_int4(c0, c1, c2, c3);
+                N[0] -= c0 + c1 + c2 + c3;
+            } else {
+                st.bad |= step_tet<SA, false, false>(d.m, mp, v.period, v.tau_k, v.tau_kf, d.seed, v.thr, t, v.S, N,
+                                                     o, &heavy, err, v.tstride, v.use_packed, pre);
+            }
         }
         if (light) st.bad |= v.template scatter<SA, kReact>(d, mp, t, sr, N, o);
     };
