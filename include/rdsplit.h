@@ -323,9 +323,11 @@ int rdsplit_engine_active(rdsplit_engine_t engine, int32_t* n_slots, int64_t* n_
 int rdsplit_engine_destroy(rdsplit_engine_t engine);
 /* Scheduling: `in_flight` simulations are processed at once (0 = as many
  * clusters as fit on the GPU at once; never more than that), each by a
- * thread-block cluster of `cluster` CTAs (1, 2 or 4; default 2) that share
- * its work through distributed shared memory.  Fewer in flight keeps their
- * working sets in L2. */
+ * thread-block cluster of `cluster` CTAs (1, 2 or 4; default 2) whose warps
+ * share its tets and meet at a cluster barrier every period.  A step's
+ * simulations are launched in groups by species count and reactions, the
+ * groups running concurrently with the in-flight clusters shared by work.
+ * Fewer in flight keeps their working sets in L2. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
 /* Slices of equal cost: with max_tet_periods > 0, rdsplit_engine_step
  * advances a simulation of T tets by min(n_steps, max(1, max_tet_periods /
