@@ -731,9 +731,34 @@ def run_serving(args, stream):
     warm = SV.Server(150e9, 8, args.slice, stream=stream)
     warm.serve([type(r)(r.rid, 0.0, r.n, r.S, r.t_end, r.model_seed) for r in small], prepared)
     warm.close()
+    # CTAs per simulation: the autotuner times the engine on the first
+    # requests of the mix (all admitted at once, one launch per cluster size)
+    tuned = None
+    cluster = args.serve_cluster
+    if cluster <= 0:
+        from paper_1512_03126_gb300 import autotune
+        dev = torch.device("cuda", torch.cuda.current_device())
+        head = reqs[:args.serve_tune_requests]
+        tsims = [rd.Simulation(prepared[r.rid].mesh, prepared[r.rid].model, stream=stream) for r in head]
+        tinit = [torch.from_numpy(np.ascontiguousarray(prepared[r.rid].counts)).to(dev) for r in head]
+
+        def treset():
+            for sm, x in zip(tsims, tinit):
+                rd.rdsplit_set_counts_device(sm.h, x)
+                rd.rdsplit_set_time(sm.h, 0.0, 0)
+
+        try:
+            tuned = autotune.tune_engine(rd, tsims, [prepared[r.rid].t_end for r in head],
+                                         [prepared[r.rid].seed for r in head], treset, stream,
+                                         clusters=(2, 4, 8), use_cache=False)
+        finally:
+            for sm in tsims:
+                sm.close()
+        cluster = tuned["best"]["cluster"]
     dense_stream = torch.cuda.Stream() if args.dense_threshold < float("inf") else None
     server = SV.Server(150e9, args.max_slots, args.slice, stream=stream, dense_threshold=args.dense_threshold,
-                       dense_stream=dense_stream, dense_lanes=args.dense_lanes, slice_work=args.slice_work)
+                       dense_stream=dense_stream, dense_lanes=args.dense_lanes, slice_work=args.slice_work,
+                       cluster=cluster)
     torch.cuda.synchronize()
     recs = server.serve(reqs, prepared)
     server.close()
@@ -756,7 +781,10 @@ def run_serving(args, stream):
                 "saturated": bool(offered and out["throughput"] and offered > 1.2 * out["throughput"]),
                 "budget_gb": 150, "slice_periods": args.slice, "slice_work_tet_periods": args.slice_work,
                 "dense_lane_threshold_tet_species": args.dense_threshold, "dense_lanes": args.dense_lanes,
-                "max_slots": args.max_slots, "serial_plain_s": serial_s,
+                "max_slots": args.max_slots, "cluster_ctas": cluster,
+                "cluster_tuning": ({"requests": args.serve_tune_requests, "results": tuned["results"]}
+                                   if tuned else None),
+                "serial_plain_s": serial_s,
                 "serial_plain_throughput": out["tet_periods"] / serial_s,
                 "throughput_vs_serial_plain": (out["throughput"] * serial_s / out["tet_periods"]),
                 "request_generation_s": round(gen_s, 1), "host_loop_s": server.host_s,
@@ -894,6 +922,10 @@ def main():
     ap.add_argument("--dense-threshold", type=float, default=float("inf"),
                     help="serving: n_tets*n_species from which a request runs in a dense lane (inf: none)")
     ap.add_argument("--dense-lanes", type=int, default=2, help="serving: dense lanes")
+    ap.add_argument("--serve-cluster", type=int, default=0,
+                    help="serving: CTAs per simulation (0: chosen by the autotuner on the first requests)")
+    ap.add_argument("--serve-tune-requests", type=int, default=100,
+                    help="serving: requests the cluster-size autotuner runs")
     ap.add_argument("--period-mode", type=int, default=0, help="dense period kernel: 0 auto, 1 one pass, 2 two passes")
     ap.add_argument("--period-block", type=int, default=0, help="dense period kernel: block size (0: by mesh size)")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-mesh workloads")

@@ -285,7 +285,7 @@ int rdsplit_get_timing(rdsplit_mesh_t mesh, double* total_ms, int64_t* n_sampled
 
 /*
  * Batched engine: many independent simulations advanced by one persistent
- * kernel in which each thread-block cluster (1, 2 or 4 CTAs, see
+ * kernel in which each thread-block cluster (1, 2, 4 or 8 CTAs, see
  * rdsplit_engine_set_concurrency) takes one simulation from a queue
  * (largest first) and runs its periods itself, touching only tets that hold
  * molecules (or have a zero-order reaction switched on).  Realisations in
@@ -323,11 +323,14 @@ int rdsplit_engine_active(rdsplit_engine_t engine, int32_t* n_slots, int64_t* n_
 int rdsplit_engine_destroy(rdsplit_engine_t engine);
 /* Scheduling: `in_flight` simulations are processed at once (0 = as many
  * clusters as fit on the GPU at once; never more than that), each by a
- * thread-block cluster of `cluster` CTAs (1, 2 or 4; default 2) whose warps
- * share its tets and meet at a cluster barrier every period.  A step's
+ * thread-block cluster of `cluster` CTAs (1, 2, 4 or 8; default 2) whose
+ * warps share its tets and meet at a cluster barrier every period.  More
+ * CTAs per simulation shorten the longest simulations (large meshes with
+ * many molecules), fewer serve more simulations at once.  A step's
  * simulations are launched in groups by species count and reactions, the
  * groups running concurrently with the in-flight clusters shared by work.
- * Fewer in flight keeps their working sets in L2. */
+ * Fewer in flight keeps their working sets in L2.  RDSPLIT_EINVAL for any
+ * other cluster size or a negative in_flight. */
 int rdsplit_engine_set_concurrency(rdsplit_engine_t engine, int32_t in_flight, int32_t cluster);
 /* Slices of equal cost: with max_tet_periods > 0, rdsplit_engine_step
  * advances a simulation of T tets by min(n_steps, max(1, max_tet_periods /

@@ -2,7 +2,7 @@
 draw is keyed by seed, period and canonical tet id, and every transfer is an
 integer sum).
 
-  engine       CTAs per simulation (1, 2 or 4) of the batched engine, at the
+  engine       CTAs per simulation (1, 2, 4 or 8) of the batched engine, at the
                number of clusters that fit on the GPU at once
   period       the dense period kernel: one pass or two passes, and the
                block size
@@ -124,7 +124,7 @@ def tune_period(rd, w, stream, periods: int = 48, candidates=None, use_cache: bo
             ms = min(_timed(dense, stream) for _ in range(2))
             results.append({"form": "dense", "mode": mode, "block": block, "ms": ms, "periods": n})
         rd.rdsplit_set_period_kernel(sim.h, 0, 0)
-        for cluster in (1, 2, 4):
+        for cluster in (1, 2, 4, 8):
             ms = []
             for _ in range(3):
                 eng = rd.rdsplit_engine_create(1, w.mesh.n_tets)
@@ -154,7 +154,7 @@ def tune_period(rd, w, stream, periods: int = 48, candidates=None, use_cache: bo
     return out
 
 
-def tune_engine(rd, sims, t_ends, seeds, reset, stream, clusters=(2, 4, 1), use_cache: bool = True,
+def tune_engine(rd, sims, t_ends, seeds, reset, stream, clusters=(2, 4, 8, 1), use_cache: bool = True,
                 shape_key: str = "") -> dict:
     """CTAs per simulation of the batched engine on the caller's ensemble:
     one full launch per candidate (after `reset()` restores the initial

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -651,9 +652,54 @@ cudaError_t launch_cluster(EngineLaunch& L) {
 
 template <int SA>
 cudaError_t launch_run_sa(bool react, int cluster, EngineLaunch& L) {
-    if (cluster >= 4) return react ? launch_cluster<SA, true, 4>(L) : launch_cluster<SA, false, 4>(L);
+    if (cluster >= 8) return react ? launch_cluster<SA, true, 8>(L) : launch_cluster<SA, false, 8>(L);
+    if (cluster == 4) return react ? launch_cluster<SA, true, 4>(L) : launch_cluster<SA, false, 4>(L);
     if (cluster == 2) return react ? launch_cluster<SA, true, 2>(L) : launch_cluster<SA, false, 2>(L);
     return react ? launch_cluster<SA, true, 1>(L) : launch_cluster<SA, false, 1>(L);
+}
+
+// Every instantiation of the engine kernel is loaded when the first engine
+// is created on a device (its attributes queried, its shared-memory limit
+// set), not at its first launch.  Under lazy module loading a step whose
+// kernel groups include a kernel not yet loaded ran its groups one after
+// another instead of concurrently (measured on the serving mix: each group
+// started when the previous one ended).
+template <int SA, bool R, int C>
+void load_kernel() {
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, k_engine_run<SA, R, C>);
+    cudaFuncSetAttribute(k_engine_run<SA, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemBytes);
+}
+
+template <int SA>
+void load_kernels_sa() {
+    load_kernel<SA, false, 1>();
+    load_kernel<SA, true, 1>();
+    load_kernel<SA, false, 2>();
+    load_kernel<SA, true, 2>();
+    load_kernel<SA, false, 4>();
+    load_kernel<SA, true, 4>();
+    load_kernel<SA, false, 8>();
+    load_kernel<SA, true, 8>();
+}
+
+void load_engine_kernels() {
+    static std::mutex mu;
+    static std::vector<int> loaded;   // devices done
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(loaded.begin(), loaded.end(), dev) != loaded.end()) return;
+    load_kernels_sa<1>();
+    load_kernels_sa<2>();
+    load_kernels_sa<4>();
+    load_kernels_sa<8>();
+    load_kernels_sa<kMaxS>();
+    cudaGetLastError();   // a failure here shows again, and is reported, at launch
+    loaded.push_back(dev);
 }
 
 }  // namespace
@@ -684,7 +730,7 @@ struct rdsplit_engine {
     cudaStream_t aux[10] = {};                // one stream per kernel group
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[10] = {};
-    int32_t cluster = 2;                      // CTAs per simulation (1, 2 or 4)
+    int32_t cluster = 2;                      // CTAs per simulation (1, 2, 4 or 8)
     std::vector<rdsplit_mesh_t> slot_mesh;    // null = free
     std::vector<SlotDesc> h_desc;
     std::vector<int32_t> slot_q;              // local periods done
@@ -784,6 +830,7 @@ int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_en
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
+    load_engine_kernels();
     if (cudaMemsetAsync(e->processed, 0, sizeof(unsigned long long), e->stream) != cudaSuccess ||
         cudaMemsetAsync(e->d_times, 0, sizeof(unsigned long long) * 4 * max_slots, e->stream) != cudaSuccess ||
         cudaMemsetAsync(e->err, 0, sizeof(uint32_t), e->stream) != cudaSuccess) {
@@ -1083,7 +1130,7 @@ int rdsplit_engine_active(rdsplit_engine_t e, int32_t* n_slots, int64_t* n_tets)
 }
 
 int rdsplit_engine_set_concurrency(rdsplit_engine_t e, int32_t in_flight, int32_t cluster) {
-    if (!e || in_flight < 0 || !(cluster == 1 || cluster == 2 || cluster == 4))
+    if (!e || in_flight < 0 || !(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8))
         return rdapi::fail(RDSPLIT_EINVAL, "rdsplit_engine_set_concurrency: bad argument");
     e->concurrency = in_flight;
     e->cluster = cluster;

@@ -9,6 +9,10 @@ join at the next slice, finished ones leave and free their memory.  A
 request's latency is its completion time minus its arrival time (queueing,
 upload, simulation and read-back included).
 
+Each simulation in the engine runs on a thread-block cluster of `cluster`
+CTAs (1, 2, 4 or 8): larger clusters shorten the largest requests, which set
+the span of a saturated mix.
+
 With `slice_work` > 0 a launch advances a large simulation by fewer periods
 (about slice_work / n_tets), so that the slices of one launch cost about
 the same and no cluster idles behind the largest request.
@@ -63,7 +67,7 @@ class Server:
 
     def __init__(self, budget_bytes: float = 150e9, max_slots: int = 128, slice_periods: int = 256,
                  stream=None, keep_counts: bool = False, dense_threshold: float = float("inf"),
-                 dense_stream=None, dense_lanes: int = 1, slice_work: int = 0):
+                 dense_stream=None, dense_lanes: int = 1, slice_work: int = 0, cluster: int = 2):
         from . import rdsplit as rd
         self.rd = rd
         self.dense_threshold = float(dense_threshold)
@@ -79,6 +83,7 @@ class Server:
         self.slice = int(slice_periods)
         self.keep_counts = keep_counts
         self.engine = rd.rdsplit_engine_create(self.max_slots, 2**31 - 1)
+        rd.rdsplit_engine_set_concurrency(self.engine, 0, int(cluster))
         if slice_work:
             rd.rdsplit_engine_set_slice_work(self.engine, int(slice_work))
         if stream is not None:

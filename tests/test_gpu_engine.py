@@ -126,7 +126,7 @@ def oracle_results(oracle):
     return [_oracle(oracle, w) for w in _workloads()]
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
 @pytest.mark.parametrize("in_flight", [1, 3, 0])
 def test_every_cluster_shape_matches_oracle(rd, oracle_results, cluster, in_flight):
     """The engine's result does not depend on how many CTAs share a
@@ -146,6 +146,21 @@ def test_every_cluster_shape_matches_oracle(rd, oracle_results, cluster, in_flig
         rd.rdsplit_engine_destroy(e)
         for s in sims:
             s.close()
+
+
+def test_cluster_sizes_other_than_1_2_4_8_are_rejected(rd):
+    e = rd.rdsplit_engine_create(1, 1000)
+    try:
+        for bad in (0, 3, 16):
+            with pytest.raises(rd.RdsplitError) as err:
+                rd.rdsplit_engine_set_concurrency(e, 0, bad)
+            assert err.value.code == rd.RDSPLIT_EINVAL
+        with pytest.raises(rd.RdsplitError):
+            rd.rdsplit_engine_set_concurrency(e, -1, 2)
+        rd.rdsplit_engine_set_concurrency(e, 0, 8)
+        assert rd.rdsplit_engine_active(e) == (0, 0)
+    finally:
+        rd.rdsplit_engine_destroy(e)
 
 
 def _stored_full_runs():
@@ -225,7 +240,7 @@ def test_deferred_queue_overflow_and_resume(rd, oracle):
     n = I.molecules(400e-6, 1e-18)
     w = I.Workload("abc_dense", m, I.abc_model(), I.place_by_volume(m, [n, n, n // 4], 6), 2e-3, 5)
     ref = _oracle(oracle, w)
-    for cluster in (1, 4):
+    for cluster in (1, 4, 8):
         with rd.Simulation(w.mesh, w.model, w.counts) as s:
             e = rd.rdsplit_engine_create(1, m.n_tets)
             try:

@@ -12,7 +12,8 @@ from paper_1512_03126_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_each_request_alone(oracle):
+@pytest.mark.parametrize("cluster", [2, 8])
+def test_served_results_equal_each_request_alone(oracle, cluster):
     import torch
     assert torch.cuda.is_available()
     from paper_1512_03126_gb300 import build
@@ -25,7 +26,7 @@ def test_served_results_equal_each_request_alone(oracle):
         w.t_end = min(w.t_end, 2e-3)
         prepared[r.rid] = w
         r.arrival = 0.002 * k          # arrivals while earlier ones run
-    srv = SV.Server(budget_bytes=2e9, max_slots=3, slice_periods=7, keep_counts=True)
+    srv = SV.Server(budget_bytes=2e9, max_slots=3, slice_periods=7, keep_counts=True, cluster=cluster)
     try:
         recs = srv.serve(reqs, prepared)
     finally:
