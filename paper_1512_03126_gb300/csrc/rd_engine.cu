@@ -658,48 +658,53 @@ cudaError_t launch_run_sa(bool react, int cluster, EngineLaunch& L) {
     return react ? launch_cluster<SA, true, 1>(L) : launch_cluster<SA, false, 1>(L);
 }
 
-// Every instantiation of the engine kernel is loaded when the first engine
-// is created on a device (its attributes queried, its shared-memory limit
-// set), not at its first launch.  Under lazy module loading a step whose
-// kernel groups include a kernel not yet loaded ran its groups one after
-// another instead of concurrently (measured on the serving mix: each group
-// started when the previous one ended).
+// Every instantiation of the engine kernel is launched once, with no work
+// items, when the first engine is created on a device: each cluster takes an
+// item index past the end and leaves, touching only the queue head (reset
+// afterwards).  A step launches one kernel per species group on concurrent
+// streams, and on the serving mix a step whose groups included kernels not
+// launched before in the process ran the groups one after another (each
+// started when the previous one ended) instead of side by side.
 template <int SA, bool R, int C>
-void load_kernel() {
-    cudaFuncAttributes a;
-    cudaFuncGetAttributes(&a, k_engine_run<SA, R, C>);
-    cudaFuncSetAttribute(k_engine_run<SA, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemBytes);
+void warm_kernel(EngineLaunch& W) {
+    if (launch_cluster<SA, R, C>(W) == cudaSuccess) note_launch();
+    cudaGetLastError();   // a failure here shows again, and is reported, at a real launch
 }
 
 template <int SA>
-void load_kernels_sa() {
-    load_kernel<SA, false, 1>();
-    load_kernel<SA, true, 1>();
-    load_kernel<SA, false, 2>();
-    load_kernel<SA, true, 2>();
-    load_kernel<SA, false, 4>();
-    load_kernel<SA, true, 4>();
-    load_kernel<SA, false, 8>();
-    load_kernel<SA, true, 8>();
+void warm_kernels_sa(EngineLaunch& W) {
+    warm_kernel<SA, false, 1>(W);
+    warm_kernel<SA, true, 1>(W);
+    warm_kernel<SA, false, 2>(W);
+    warm_kernel<SA, true, 2>(W);
+    warm_kernel<SA, false, 4>(W);
+    warm_kernel<SA, true, 4>(W);
+    warm_kernel<SA, false, 8>(W);
+    warm_kernel<SA, true, 8>(W);
 }
 
-void load_engine_kernels() {
+// head: int32[kGroups] of the engine being created (left zero); err and
+// processed: its error word and entry counter (not written: no item runs).
+void warm_engine_kernels(int32_t* head, uint32_t* err, unsigned long long* processed, int sms) {
     static std::mutex mu;
-    static std::vector<int> loaded;   // devices done
+    static std::vector<int> warmed;   // devices done
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return;
     }
     std::lock_guard<std::mutex> lock(mu);
-    if (std::find(loaded.begin(), loaded.end(), dev) != loaded.end()) return;
-    load_kernels_sa<1>();
-    load_kernels_sa<2>();
-    load_kernels_sa<4>();
-    load_kernels_sa<8>();
-    load_kernels_sa<kMaxS>();
-    cudaGetLastError();   // a failure here shows again, and is reported, at launch
-    loaded.push_back(dev);
+    if (std::find(warmed.begin(), warmed.end(), dev) != warmed.end()) return;
+    EngineLaunch W{nullptr, nullptr, nullptr, 0, head, err, processed, nullptr, (cudaStream_t)0, sms, 1};
+    warm_kernels_sa<1>(W);
+    warm_kernels_sa<2>(W);
+    warm_kernels_sa<4>(W);
+    warm_kernels_sa<8>(W);
+    warm_kernels_sa<kMaxS>(W);
+    cudaMemsetAsync(head, 0, sizeof(int32_t) * 10, (cudaStream_t)0);
+    cudaStreamSynchronize((cudaStream_t)0);
+    cudaGetLastError();
+    warmed.push_back(dev);
 }
 
 }  // namespace
@@ -830,7 +835,7 @@ int rdsplit_engine_create(int32_t max_slots, int64_t max_active_tets, rdsplit_en
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
-    load_engine_kernels();
+    warm_engine_kernels(e->d_head, e->err, e->processed, e->sms);
     if (cudaMemsetAsync(e->processed, 0, sizeof(unsigned long long), e->stream) != cudaSuccess ||
         cudaMemsetAsync(e->d_times, 0, sizeof(unsigned long long) * 4 * max_slots, e->stream) != cudaSuccess ||
         cudaMemsetAsync(e->err, 0, sizeof(uint32_t), e->stream) != cudaSuccess) {
