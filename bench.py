@@ -424,7 +424,7 @@ def run_ensemble(args, rank, world, local_rank):
                  "form": "one rdsplit_run launch sequence per simulation (dense period kernel)"}
 
     # the plain engine form: the same engine, one simulation per launch
-    # (4-CTA clusters, the fastest single-simulation shape), on every 8th
+    # (4-CTA clusters, the fastest of 1, 2 and 4 CTAs for one simulation), on every 8th
     # instance; separates the gain of batching from that of skipping empty tets
     plain_engine = None
     if rank == 0 and not args.no_plain:

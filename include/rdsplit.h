@@ -296,6 +296,10 @@ int rdsplit_get_timing(rdsplit_mesh_t mesh, double* total_ms, int64_t* n_sampled
  *
  * rdsplit_engine_create: max_slots simultaneous simulations; max_active_tets
  *   bounds the sum of n_tets over simulations in the engine (admission limit).
+ *   The first engine created on a device launches every engine kernel once
+ *   with no work, on the legacy default stream, and waits for them (so that
+ *   the concurrent group launches of a step never wait on a first launch);
+ *   create it before any stream capture.
  * rdsplit_engine_add: a mesh handle with its model and counts joins; it will
  *   run from its current time to t_end with `seed` (as rdsplit_run would).
  *   RDSPLIT_ENOMEM if no slot or capacity is free.  The handle must not be
