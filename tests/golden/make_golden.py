@@ -4,6 +4,12 @@ at full size can be checked without rerunning the oracle for minutes.
 
 Calls only ``oracle/`` and the seeded input generators.  Usage:
     python tests/golden/make_golden.py [name ...]
+    python tests/golden/make_golden.py --check [--max-seconds S] [name ...]
+The second form writes nothing: it reruns the stored entries (those named,
+else every one whose recorded oracle time is at most S seconds, default 3)
+with the oracle built on this host and compares their digests with the
+stored ones, so that the oracle's bit-identity across hosts (x86-64 and
+aarch64) can be checked; it exits 1 on any mismatch.
 """
 from __future__ import annotations
 
@@ -115,5 +121,31 @@ def main(names):
             print(name, rec["oracle_seconds"], "s", flush=True)
 
 
+def check(names, max_seconds: float) -> int:
+    from oracle import build
+    build.build()
+    stored = json.load(open(OUT))
+    todo = entries()
+    pick = names or [k for k, v in stored.items() if v["oracle_seconds"] <= max_seconds]
+    order = [(k, todo[k]) for k in sorted(pick) if k in todo and k in stored]
+    bad = 0
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(8, os.cpu_count() or 1)) as pool:
+        for name, rec in pool.imap_unordered(run_entry, order):
+            ok = rec["sha256"] == stored[name]["sha256"]
+            bad += 0 if ok else 1
+            print(name, "same" if ok else "DIFFERENT", flush=True)
+    print(f"{len(order) - bad} of {len(order)} stored runs reproduced on this host", flush=True)
+    return 1 if bad else 0
+
+
 if __name__ == "__main__":
-    main(sys.argv[1:])
+    argv = sys.argv[1:]
+    if argv and argv[0] == "--check":
+        argv = argv[1:]
+        limit = 3.0
+        if len(argv) >= 2 and argv[0] == "--max-seconds":
+            limit = float(argv[1])
+            argv = argv[2:]
+        sys.exit(check(argv, limit))
+    main(argv)
