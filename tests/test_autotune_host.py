@@ -22,3 +22,70 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     A.cache_put("y", {"best": {"mode": 1, "block": 128}})
     assert A.cache_get("x") == {"best": {"cluster": 2}}
     assert A.cache_get("y")["best"]["block"] == 128
+
+
+class _FakeEngineRd:
+    """Stands in for the binding: records the cluster size of each engine and
+    lets the timing stub report a cost per cluster size."""
+
+    def __init__(self):
+        self.cluster = {}
+        self.launched = []
+        self.destroyed = 0
+
+    def rdsplit_get_shape(self, h):
+        return (100, 1)
+
+    def rdsplit_engine_create(self, n, cap):
+        e = object()
+        self.cluster[e] = None
+        return e
+
+    def rdsplit_engine_set_stream(self, e, s):
+        pass
+
+    def rdsplit_engine_set_concurrency(self, e, in_flight, cluster):
+        assert in_flight == 0
+        self.cluster[e] = cluster
+
+    def rdsplit_engine_add(self, e, h, t_end, seed):
+        pass
+
+    def rdsplit_engine_step(self, e, n):
+        self.launched.append(self.cluster[e])
+
+    def rdsplit_engine_poll(self, e, n):
+        return []
+
+    def rdsplit_engine_schedule(self, e):
+        c = self.cluster[e]
+        return (152 // c, c, 152 // c)
+
+    def rdsplit_engine_destroy(self, e):
+        self.destroyed += 1
+
+
+def test_tune_engine_times_every_cluster_size_and_keeps_the_fastest(tmp_path, monkeypatch):
+    import types
+    monkeypatch.setenv("RDSPLIT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(A, "_device_name", lambda: "fake-gpu")
+    cost = {1: 9.0, 2: 4.0, 4: 2.5, 8: 3.0}
+    rd = _FakeEngineRd()
+
+    def timed(fn, stream):
+        fn()
+        return cost[rd.launched[-1]]
+
+    monkeypatch.setattr(A, "_timed", timed)
+    resets = []
+    sims = [types.SimpleNamespace(h=i) for i in range(3)]
+    out = A.tune_engine(rd, sims, [0.1] * 3, [1, 2, 3], lambda: resets.append(1), None,
+                        clusters=(2, 4, 8, 1), use_cache=True, shape_key="mix")
+    assert rd.launched == [2, 4, 8, 1] and len(resets) == 4 and rd.destroyed == 4
+    assert out["best"] == {"cluster": 4}
+    assert [r["cluster"] for r in out["results"]] == [2, 4, 8, 1]
+    assert out["results"][1]["in_flight"] == 38
+    # a second call with the same shape key comes from the cache
+    again = A.tune_engine(rd, sims, [0.1] * 3, [1, 2, 3], lambda: resets.append(1), None,
+                          clusters=(2, 4, 8, 1), use_cache=True, shape_key="mix")
+    assert again["cached"] and again["best"] == {"cluster": 4} and len(rd.launched) == 4

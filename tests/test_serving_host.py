@@ -204,3 +204,18 @@ def test_dense_lane_error_is_raised():
     with pytest.raises(RuntimeError, match="request 2 failed"):
         srv.serve([p[0] for p in pairs], {p[0].rid: p[1] for p in pairs})
     assert srv.used == 0
+
+
+def test_server_sets_the_engine_cluster_size(monkeypatch):
+    from paper_1512_03126_gb300 import rdsplit as rd
+    calls = []
+    monkeypatch.setattr(rd, "rdsplit_engine_create", lambda n, cap: "eng")
+    monkeypatch.setattr(rd, "rdsplit_engine_set_concurrency", lambda e, f, c: calls.append(("conc", e, f, c)))
+    monkeypatch.setattr(rd, "rdsplit_engine_set_slice_work", lambda e, w: calls.append(("work", e, w)))
+    monkeypatch.setattr(rd, "rdsplit_engine_destroy", lambda e: calls.append(("destroy", e)))
+    srv = SV.Server(budget_bytes=1e9, max_slots=4, cluster=8, slice_work=1000)
+    srv.close()
+    assert calls == [("conc", "eng", 0, 8), ("work", "eng", 1000), ("destroy", "eng")]
+    calls.clear()
+    SV.Server(budget_bytes=1e9, max_slots=4).close()
+    assert calls == [("conc", "eng", 0, 2), ("destroy", "eng")]
