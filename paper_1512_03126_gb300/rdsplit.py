@@ -347,7 +347,7 @@ def rdsplit_set_transfer_rule(h, rule: int):
     _check(lib().rdsplit_set_transfer_rule(h, int(rule)))
 
 
-def rdsplit_engine_set_concurrency(e, in_flight: int, cluster: int = 4):
+def rdsplit_engine_set_concurrency(e, in_flight: int, cluster: int):
     _check(lib().rdsplit_engine_set_concurrency(e, int(in_flight), int(cluster)))
 
 
