@@ -8,9 +8,11 @@ through a cut face land in the inbox slot 4 u + r of a tet u of another
 rank (face r of u); `cut_slots` lists those slots, in increasing order, for
 one (sender, receiver) pair of ranges: the sender exports them after each
 period and the receiver imports them, in the same order, before the next.
-`run_rank` drives one rank of a partitioned run through the library (the
-exchange itself is the caller's: host or NCCL send/receive).  No method
-arithmetic lives here: every period runs in the library's kernels.
+`run_rank` drives one rank of a partitioned run through the library; the
+exchange itself is the caller's, and `p2p_exchange` gives one over
+torch.distributed point-to-point operations (NCCL between GPUs, with the
+buffers left on the device).  No method arithmetic lives here: every period
+runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -69,3 +71,35 @@ def run_rank(rd, h, adj, rank: int, parts: list, t_end: float, seed: int, exchan
             rd.rdsplit_inbox_import(h, sl, recvs[p])
     rd.rdsplit_partition_end(h)
     return periods
+
+
+def p2p_exchange(dist, device=None):
+    """An `exchange` for run_rank over torch.distributed point-to-point
+    operations.  All sends and receives of one period are posted in one
+    batch (batch_isend_irecv, one NCCL group between GPUs, so that two ranks
+    sending to each other do not wait on each other's order) and completed
+    before it returns.  A receive lands in a new int32 tensor on `device`
+    (default: the current CUDA device, else the CPU).  With NCCL, completion
+    orders the current torch stream after the transfers: the library's
+    stream must be that stream (the default), or be synchronised with it,
+    before rdsplit_inbox_import reads the buffers."""
+    import torch
+
+    def exchange(sends, recv_shapes):
+        dev = device
+        if dev is None:
+            dev = (torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available()
+                   else torch.device("cpu"))
+        ops, recvs = [], {}
+        for p in sorted(set(sends) | set(recv_shapes)):
+            if p in recv_shapes:
+                recvs[p] = torch.empty(tuple(recv_shapes[p]), dtype=torch.int32, device=dev)
+                ops.append(dist.P2POp(dist.irecv, recvs[p], p))
+            if p in sends:
+                ops.append(dist.P2POp(dist.isend, sends[p].contiguous(), p))
+        if ops:
+            for req in dist.batch_isend_irecv(ops):
+                req.wait()
+        return recvs
+
+    return exchange

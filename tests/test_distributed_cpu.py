@@ -7,7 +7,9 @@
    advances its own contiguous range of tets for a period (the oracle's
    per-range Steps 2-3), the transfers across cut faces (and only those) go
    to the rank that owns the receiving tet once per period, in the order of
-   partition.cut_slots, and each rank applies what its tets receive.  Because every draw is keyed by
+   partition.cut_slots, through partition.p2p_exchange (the exchange the
+   library offers for NCCL between GPUs, here over gloo), and each rank
+   applies what its tets receive.  Because every draw is keyed by
    the canonical tet id, the result must equal the single-process run bit
    for bit, for any number of ranks.
 """
@@ -91,6 +93,7 @@ def _dd_worker(rank, world, port, outpath):
     face_to = lambda t, u: int(np.nonzero(adj[t] == u)[0][0])
     sends = {p: P.cut_slots(adj, (lo, hi), parts[p]) for p in range(world) if p != rank}
     recvs = {p: P.cut_slots(adj, parts[p], (lo, hi)) for p in range(world) if p != rank}
+    exchange = P.p2p_exchange(dist, torch.device("cpu"))
     N = np.zeros((T, S), np.int32)
     N[lo:hi] = w.counts[lo:hi]            # a rank holds only its own tets
     tau = O.tau(w.mesh, w.model)
@@ -101,25 +104,24 @@ def _dd_worker(rank, world, port, outpath):
             tau_k, last = w.t_end - t_now, True
         out, rem = O.period_tets(w.mesh, w.model, N, period, tau_k, w.seed, lo, hi)
         # the one exchange of the period: the transfers across cut faces
-        # only, to the rank that owns the receiving tet
-        reqs, got = [], {}
+        # only, to the rank that owns the receiving tet (the library's
+        # point-to-point exchange, here over gloo with host tensors)
+        bufs = {}
         for p, sl in sends.items():
+            if not len(sl):
+                continue
             buf = np.zeros((len(sl), S), np.int32)
             for k, slot in enumerate(sl):
                 u, r = divmod(int(slot), 4)
                 t = int(adj[u, r])
                 buf[k] = out[t - lo, :, face_to(t, u)]
-            reqs.append(dist.isend(torch.from_numpy(buf), dst=p))
-        for p, sl in recvs.items():
-            got[p] = torch.zeros((len(sl), S), dtype=torch.int32)
-            reqs.append(dist.irecv(got[p], src=p))
-        for q in reqs:
-            q.wait()
+            bufs[p] = torch.from_numpy(buf)
+        got = exchange(bufs, {p: (len(sl), S) for p, sl in recvs.items() if len(sl)})
         incoming = np.zeros((T, S), np.int64)
-        for p, sl in recvs.items():
-            for k, slot in enumerate(sl):
+        for p, x in got.items():
+            for k, slot in enumerate(recvs[p]):
                 u = int(slot) // 4
-                incoming[u] += got[p].numpy()[k]
+                incoming[u] += x.numpy()[k]
         # synchronous apply for this rank's tets
         N[:] = 0
         for t in range(lo, hi):
